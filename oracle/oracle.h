@@ -1,0 +1,94 @@
+/*
+ * Swarm-NG method oracle — plain, single-threaded FP64 CPU restatement of the
+ * integrators of Dindar et al., "Swarm-NG: a CUDA library for parallel n-body
+ * integrations with focus on simulations of planetary systems" (arXiv:1208.1157).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline leg of
+ * the benchmark call this code; the library's product path never does.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Units: G = 1 (Sec. 2.1, Eq. 1), AU, solar masses, one year = 2 pi.
+ * Layout: one system at a time, body b at x[3*b + c] (c = 0, 1, 2); body 0 is the
+ * central mass.  Every function is a direct transcription of the passage it cites.
+ */
+#ifndef SWARM_ORACLE_H
+#define SWARM_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* per-system outcome codes (monitor of Sec. 4.3, Algorithm 1) */
+enum { OR_ACTIVE = 0, OR_DONE = 1, OR_CLOSE_ENCOUNTER = 2, OR_EJECTED = 3,
+       OR_KEPLER_NOCONV = 4, OR_NONFINITE = 5 };
+/* integrators */
+enum { OR_HERMITE = 1, OR_MVS_DH = 2, OR_MVS_JACOBI = 3 };
+/* Hermite corrector forms: the time-symmetric form of Kokubo et al. 1998 cited in
+ * Sec. 2.2.1, and the printed Eq. 4 read with 3/20 and the predicted base. */
+enum { OR_CORR_KOKUBO = 0, OR_CORR_PRINTED = 1 };
+
+/* Eq. 1 and its time derivative, ordered pairs, star (j = 0) accumulated last. */
+void or_accjerk(int n, const double *m, const double *x, const double *v, double *a, double *jerk);
+/* Eq. 1 alone. */
+void or_acc(int n, const double *m, const double *x, double *a);
+
+/* One Hermite step (Eq. 3 predictor, n_corr correctors, Algorithm 2) followed by
+ * the evaluation at the corrected state that gives the next step's a0, j0. */
+void or_hermite_step(int n, const double *m, double *x, double *v, double *a0, double *j0,
+                     double dt, int n_corr, int form);
+
+/* Eq. 6 energy (pairs counted once) and total angular momentum L[3]. */
+void or_energy(int n, const double *m, const double *x, const double *v, double *E, double *L);
+
+/* Stop conditions on inertial x, v: NONFINITE, EJECTED (heliocentric distance
+ * above eject_radius), CLOSE_ENCOUNTER (planet pair closer than ce_factor mutual
+ * Hill radii); a test is off when its parameter is <= 0.  Returns OR_ACTIVE if none. */
+int or_monitor(int n, const double *m, const double *x, const double *v, double ce_factor, double eject_radius);
+
+/* Stumpff functions c2(z), c3(z) (closed forms; Taylor series for |z| < 1). */
+void or_stumpff(double z, double *c2, double *c3);
+/* Universal-variable Kepler drift of one two-body orbit (r, v) by dt with
+ * gravitational parameter mu; Newton on the universal Kepler equation.
+ * Returns 0, or OR_KEPLER_NOCONV after 50 iterations.  *iters gets the count. */
+int or_kepler_drift(double mu, double *r, double *v, double dt, int *iters);
+
+/* MVS coordinate maps (Sec. 2.2.3).  Democratic heliocentric: q[0] = centre of mass,
+ * q[i] = x_i - x_0; u[0] = centre-of-mass velocity, u[i] = v_i - v_cm (= P_i/m_i). */
+void or_inertial_to_dh(int n, const double *m, const double *x, const double *v, double *q, double *u);
+void or_dh_to_inertial(int n, const double *m, const double *q, const double *u, double *x, double *v);
+/* Jacobi: r[0] = centre of mass, r[i] = x_i - (centre of mass of bodies 0..i-1). */
+void or_inertial_to_jacobi(int n, const double *m, const double *x, const double *v, double *r, double *w);
+void or_jacobi_to_inertial(int n, const double *m, const double *r, const double *w, double *x, double *v);
+
+/* One full MVS step in the paper's sub-step order; acc is the planet-planet
+ * (DH) or interaction (Jacobi) acceleration cache, valid on entry for the current
+ * positions and refreshed after the Kepler drift.  Returns 0 or OR_KEPLER_NOCONV. */
+int or_mvs_dh_step(int n, const double *m, double *q, double *u, double *acc, double dt);
+int or_mvs_jacobi_step(int n, const double *m, double *r, double *w, double *acc, double dt);
+void or_dh_interaction_acc(int n, const double *m, const double *q, double *acc);
+void or_jacobi_interaction_acc(int n, const double *m, const double *r, double *acc);
+
+/* Integrate one system from *t to t_end (Algorithm 1 with a monitor after every
+ * step).  Step count: N = round(D) when D = (t_end - t)/dt is within 1e-9 of an
+ * integer, else ceil(D) with the last step shortened to land on t_end.  Systems whose
+ * status is a stop code (>= 2) are left untouched.  Every log_interval steps (0 = off)
+ * one record (t, E, Lx, Ly, Lz) is appended to log (capacity log_cap records). */
+typedef struct {
+  int integrator, n_corr, corr_form, log_interval, log_cap;
+  double ce_factor, eject_radius;
+} or_params;
+int or_integrate(int n, const double *m, double *x, double *v, double *t, int *status,
+                 double t_end, double dt, const or_params *p, double *log, int *log_count,
+                 long long *kepler_iters);
+
+/* Ensemble wrapper: systems back to back (n_body[s] bodies each).  log is
+ * [n_sys][log_cap][5], log_count [n_sys]; either may be NULL when log_interval = 0. */
+int or_integrate_ensemble(int n_sys, const int *n_body, const double *mass, double *pos, double *vel,
+                          double *time, int *status, double t_end, double dt, int integrator,
+                          int n_corr, int corr_form, double ce_factor, double eject_radius,
+                          int log_interval, int log_cap, double *log, int *log_count,
+                          long long *kepler_iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
