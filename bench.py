@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 ensemble integrator on GB300.
+
+One bench step = one swarm_integrate call advancing the paper-shaped ensemble
+(131072 systems x 3 bodies, Hermite-4 P(EC)^2, dt = 1e-3 inner periods) by 10^4 steps
+with energy/angular-momentum logging every 1000 steps and the close-encounter /
+ejection monitor on.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank integrates its own independent ensemble (weak scaling, no
+collective on the data path; the barrier and the max over ranks are for timing only).
+--impl reference times the CPU oracle (plain single-threaded C, one process per host
+core) on a bounded sample of the same workload.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TWO_PI = 2.0 * math.pi
+DT = TWO_PI * 1e-3
+N_SYS = 131072
+N_BODY = 3
+STEPS_PER_CALL = 10000
+LOG_EVERY = 1000
+METRIC = "FP64 system-steps/s & pair-interactions/s vs FP64 peak; serving p50/p99 latency"
+WORKLOAD = "paper-shaped ensemble: 131072 systems x 3 bodies (seed 2), Hermite-4 P(EC)^2 FP64, 10^4 steps per call, dt = 2pi 1e-3, E/L logged every 1000 steps, stops on (3 Hill radii, 100 AU)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ operation counts
+def hermite_flops_per_system_step(n, n_corr=2):
+    """FP64 operations of the implemented Hermite step (a DFMA counts 2, rsqrt 1).
+
+    per unique pair and evaluation: 6 differences, 2 dot products (2 x 5), rsqrt (1),
+    rho^2, rho^3 (2), -3 (r.u) rho^2 (2), w = dv + c dx (3 DFMA = 6), each body's share
+    (1 DMUL + 6 DFMA = 13, twice) = 53; n_corr + 1 evaluations per step.
+    per body component and step: predictor 5 DFMA, corrector bases 4 DFMA, 4 DFMA per
+    corrector pass: (9 + 4 n_corr) * 2 flops."""
+    P = n * (n - 1) // 2
+    return (n_corr + 1) * P * 53 + 3 * n * (9 + 4 * n_corr) * 2
+
+
+def source_hash(patterns):
+    h = hashlib.sha256()
+    for p in sorted(sum((glob.glob(os.path.join(ROOT, q)) for q in patterns), [])):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+HERMITE_SOURCES = ["paper_1208_1157_gb300/csrc/hermite*.cu*", "paper_1208_1157_gb300/csrc/common.cuh"]
+
+
+def traffic_per_launch(kernel, systems):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `systems`, or None
+    when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel)
+        if not d or d.get("source_hash") != source_hash(HERMITE_SOURCES):
+            return None
+        return d["dram_bytes_per_system"] * systems
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception as ex:  # no nvidia-smi: report unknown clocks
+            log("clock sampling unavailable:", ex)
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 250.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def _oracle_chunk(args):
+    seed, idx, steps = args
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_1208_1157_gb300 import ics
+
+    ens = ics.subset(ics.three_body(int(max(idx)) + 1, seed), idx)
+    t = time.perf_counter()
+    O.integrate(ens, steps * DT, DT, O.HERMITE, ce_factor=3.0, eject_radius=100.0)
+    return time.perf_counter() - t
+
+
+def oracle_throughput(target_s=15.0, steps=STEPS_PER_CALL, seed=2):
+    """The oracle as it stands, one process per host core (spawned before any CUDA use),
+    on a sample of systems sized for about target_s seconds of wall time."""
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        # calibrate: one system for 1000 steps on one core
+        t1 = pool.map(_oracle_chunk, [(seed, [0], 1000)])[0]
+        per_sys = t1 * steps / 1000.0
+        per_core = max(1, int(target_s / max(per_sys, 1e-6)))
+        S = min(cores * per_core, N_SYS)
+        chunks = [(seed, list(range(c, S, cores)), steps) for c in range(cores) if c < S]
+        t = time.perf_counter()
+        pool.map(_oracle_chunk, chunks)
+        wall = time.perf_counter() - t
+    return {"value": S * steps / wall, "unit": "system-steps/s", "cores": min(cores, S), "kind": "oracle",
+            "sample": f"{S} of the {N_SYS} systems (seed 2), {steps} Hermite steps each, one process per core",
+            "wall_s": wall}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    res = None
+    for k in range(args.warmup + args.steps):
+        res = oracle_throughput(target_s=args.ref_seconds)
+        if k >= args.warmup:
+            per_step.append(res)
+    value = statistics.median(r["value"] for r in per_step)
+    cpu = dict(per_step[-1])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "system-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(r["wall_s"] for r in per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": cpu["sample"]},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": "system-steps/s", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our path
+def secondary(S, torch, stream):
+    """Short measurements of the other rows of the hot path (not the headline value)."""
+    from paper_1208_1157_gb300 import ics
+
+    out = {}
+
+    def timed(ens, t_end, integ, dt, mapping=0, ce=3.0, ej=100.0):
+        with S.Ensemble(ens, stream=stream) as e:
+            e.set_option(S.OPT_MAPPING, mapping)
+            e.set_stop(ce, ej)
+            e.integrate(min(t_end, 2 * dt), integ, dt)  # warm-up (tuner, caches)
+            e.set_state(ens["pos"], ens["vel"], time=[0.0] * len(ens["n_body"]),
+                        status=[0] * len(ens["n_body"]))
+            e.integrate(t_end, integ, dt)
+            st = e.stats()
+        sec = st["kernel_ms"] * 1e-3
+        return {"system_steps_per_s": st["system_steps"] / sec, "pair_interactions_per_s": st["pair_evaluations"] / sec,
+                "kernel_ms": st["kernel_ms"], "launches": st["kernel_launches"], "system_steps": st["system_steps"],
+                "kepler_iterations": st["kepler_iterations"]}
+
+    c2 = ics.three_body(N_SYS, seed=2)
+    out["c2_plain_one_launch_per_step_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_PLAIN_PER_STEP)
+    c1 = ics.three_body(1024, seed=1)
+    out["c1_plain_one_launch_per_step_1000"] = timed(c1, 1000 * DT, S.HERMITE4, DT, mapping=S.MAP_PLAIN_PER_STEP)
+    out["c1_persistent_1000"] = timed(c1, 1000 * DT, S.HERMITE4, DT)
+    out["c2_persistent_500"] = timed(c2, 500 * DT, S.HERMITE4, DT)
+    out["c2_persistent_body_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_BODY_PER_LANE)
+    out["c2_persistent_system_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE)
+    c3 = ics.ragged(65536, seed=3)
+    out["c3_ragged_hermite_single_launch_4_steps"] = timed(c3, 4 * DT, S.HERMITE4, DT)
+    c4 = ics.mvs_compact(16384, seed=4)
+    out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
+    out["c4_mvs_dh_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20)
+    return out
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # CPU baseline first: the oracle's process pool is spawned before any CUDA use
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_throughput(target_s=args.cpu_seconds)
+        log(f"cpu baseline: {cpu['value']:.3e} system-steps/s on {cpu['cores']} cores")
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1208_1157_gb300 import ics
+    from paper_1208_1157_gb300 import swarm as S
+
+    stream = torch.cuda.current_stream()
+    peak = S.fp64_peak(0.5, stream)
+    log(f"measured FP64 peak {peak / 1e12:.4f} TFLOP/s")
+    ens = ics.three_body(N_SYS, seed=2 + 1000 * rank)
+    T = STEPS_PER_CALL * DT
+    e = S.Ensemble(ens, stream=stream)
+    e.set_stop(3.0, 100.0)
+    e.set_option(S.OPT_LOG_CAPACITY, 64)
+    e.set_option(S.OPT_LOG_INTERVAL, LOG_EVERY)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    t = 0.0
+    for _ in range(args.warmup):
+        t += T
+        e.integrate(t, S.HERMITE4, DT)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    t0 = time.perf_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    steps_done = pairs_done = 0
+    kernel_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        t += T
+        ev[k][0].record(stream)
+        e.integrate(t, S.HERMITE4, DT)
+        ev[k][1].record(stream)
+        st = e.stats()
+        steps_done += st["system_steps"]
+        pairs_done += st["pair_evaluations"]
+        kernel_ms.append(st["kernel_ms"])
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        tt = torch.tensor([ms, wall * 1e3, steps_done, pairs_done], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms = float(mx[0])
+        steps_total, pairs_total = float(sm[2]), float(sm[3])
+    else:
+        steps_total, pairs_total = float(steps_done), float(pairs_done)
+    sec = ms * 1e-3
+    value = steps_total / sec
+
+    # ---- end to end through the C ABI with pinned host buffers, copies inside the region
+    pos_h = torch.empty((e.n_bodies, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vel_h = torch.empty((e.n_bodies, 3), dtype=torch.float64, pin_memory=True).numpy()
+    tim_h = torch.empty(e.n_sys, dtype=torch.float64, pin_memory=True).numpy()
+    sta_h = torch.empty(e.n_sys, dtype=torch.int32, pin_memory=True).numpy()
+    e.state_into(pos_h, vel_h, tim_h, sta_h)
+    barrier()
+    e2e_t0 = time.perf_counter()
+    e2e_steps = 0
+    for k in range(args.steps):
+        flush.zero_()
+        t += T
+        e.set_state(pos_h, vel_h, tim_h, sta_h)
+        e.integrate(t, S.HERMITE4, DT)
+        e2e_steps += e.stats()["system_steps"]
+        e.state_into(pos_h, vel_h, tim_h, sta_h)
+    barrier()
+    e2e_wall = time.perf_counter() - e2e_t0
+    if dist:
+        tt = torch.tensor([e2e_wall, e2e_steps], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        e2e_wall, e2e_steps = float(mx[0]), float(sm[1])
+    bytes_io = pos_h.nbytes + vel_h.nbytes + tim_h.nbytes + sta_h.nbytes
+
+    fl = hermite_flops_per_system_step(N_BODY)
+    launch_ms = statistics.mean(kernel_ms)
+    flops_per_launch = fl * steps_done / args.steps
+    achieved = flops_per_launch / (launch_ms * 1e-3)
+    traffic = traffic_per_launch("hermite_persistent_kernel", N_SYS)
+    sec_out = {}
+    if rank == 0 and not args.no_secondary:
+        sec_out = secondary(S, torch, stream)
+    e.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "system-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded planetary ICs, no dataset)",
+        "config": {"workload": WORKLOAD, "n_sys_per_gpu": N_SYS, "n_body": N_BODY, "steps_per_call": STEPS_PER_CALL,
+                   "dt": DT, "l2": "256 MB buffer written before every timed step (state is 22 MB < L2)",
+                   "parallelism": f"replicas x{world} (independent ensembles, no collective)"},
+        "pair_interactions_per_s": pairs_total / sec,
+        "fp64_flops_per_system_step": fl,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "hermite_persistent_kernel",
+                     "peak_kind": "measured DFMA-chain peak on this GPU (2 flops per DFMA)",
+                     "avg_launch_ms": launch_ms},
+        "e2e": {"value": e2e_steps / e2e_wall, "unit": "system-steps/s", "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "paper_context": {"system_steps_per_s_tesla_c2070_derived": 4.47e6,
+                          "note": "131072 x 3 Hermite, Table 3, 1 time unit at dt=1e-3; other hardware"},
+        "secondary": sec_out,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ncu_case(name):
+    """One small fixed run of a kernel, for Nsight Compute captures (no timing)."""
+    import torch
+
+    from paper_1208_1157_gb300 import ics
+    from paper_1208_1157_gb300 import swarm as S
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if name in ("hermite", "hermite_bpl", "plain"):
+        ens = ics.three_body(N_SYS, seed=2)
+        mapping = {"hermite": S.MAP_SYSTEM_PER_LANE, "hermite_bpl": S.MAP_BODY_PER_LANE, "plain": S.MAP_PLAIN_PER_STEP}[name]
+        steps, integ, dt = (200 if name != "plain" else 20), S.HERMITE4, DT
+    elif name == "mvs":
+        ens = ics.mvs_compact(16384, seed=4)
+        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 200, S.MVS_JACOBI, TWO_PI / 20
+    elif name == "ragged":
+        ens = ics.ragged(65536, seed=3)
+        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 2, S.HERMITE4, DT
+    else:
+        raise SystemExit(f"unknown case {name}")
+    with S.Ensemble(ens, stream=stream) as e:
+        e.set_option(S.OPT_MAPPING, mapping)
+        e.set_stop(3.0, 100.0)
+        e.integrate(steps * dt, integ, dt)
+        st = e.stats()
+    log(f"ncu case {name}: {st}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged"])
+    args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args.ncu_case)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * swarm.h — C ABI of a GB300 (sm_103a) library that advances large ensembles of
+ * independent few-body gravitational systems (2..15 bodies each) in FP64, with the
+ * two integrators of Swarm-NG (Dindar et al., arXiv:1208.1157):
+ *   - the 4th-order time-symmetric Hermite predict-evaluate-correct step (Sec. 2.2.1,
+ *     Eq. 3 predictor, Eq. 4 corrector read in the time-symmetric form of Kokubo et
+ *     al. 1998, Algorithm 2, two corrector passes, three force evaluations per step);
+ *   - the mixed-variable symplectic step (Sec. 2.2.3, Sec. 4.3.4) in democratic
+ *     heliocentric or Jacobi coordinates, with a universal-variable Kepler drift.
+ * The multi-step loop runs on the device (Algorithm 1, Sec. 5.3): one call advances
+ * every system to t_end with a monitor after each step.
+ *
+ * Conventions for every entry point:
+ *  - Units: G = 1 (Eq. 1); AU, solar masses, one year = 2 pi time units.
+ *  - Bodies are stored system after system, body 0 of each system being the central
+ *    mass (Sec. 4.2); positions/velocities are [sum(n_body)][3] row-major doubles in an
+ *    inertial frame.
+ *  - Return codes are SWARM_OK or a negative SWARM_E*; no exception crosses the ABI.
+ *    swarm_last_error() gives a message for the calling thread's last failure.
+ *    Per-system outcomes are reported in a status array, not in the return code.
+ *  - Host pointers are caller-owned and only read/written during the call (copies in
+ *    and out).  "_dev" entry points take device pointers on the ensemble's stream.
+ *  - The ensemble owns its device memory from create to destroy; it is not
+ *    thread-safe: one thread at a time may use a given ensemble.
+ *  - Every CUDA error in a call is reported as SWARM_ECUDA; the ensemble should then
+ *    be destroyed.
+ */
+#ifndef SWARM_GB300_H
+#define SWARM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+enum swarm_rc {
+  SWARM_OK = 0,
+  SWARM_EINVAL = -1,   /* bad argument (sizes, ranges, non-finite input, dt = 0) */
+  SWARM_ENOMEM = -2,   /* device or host allocation failed */
+  SWARM_ECUDA = -3,    /* a CUDA runtime call or kernel failed */
+  SWARM_ETIMEOUT = -4, /* a bounded device wait gave up */
+  SWARM_ESTATE = -5    /* call not valid in the object's current state */
+};
+
+enum swarm_integrator {
+  SWARM_HERMITE4 = 1,   /* Sec. 2.2.1 / Algorithm 2 */
+  SWARM_MVS_DH = 2,     /* Sec. 2.2.3, democratic heliocentric, five sub-steps */
+  SWARM_MVS_JACOBI = 3  /* Wisdom & Holman 1991 map in Jacobi coordinates */
+};
+
+/* per-system status (the monitor of Sec. 4.3, Algorithm 1) */
+enum swarm_sys_status {
+  SWARM_SYS_ACTIVE = 0,          /* runnable, has not been integrated yet */
+  SWARM_SYS_DONE = 1,            /* reached the last call's t_end; still runnable */
+  SWARM_SYS_CLOSE_ENCOUNTER = 2, /* two planets closer than ce_factor mutual Hill radii */
+  SWARM_SYS_EJECTED = 3,         /* a planet farther than eject_radius from the central body */
+  SWARM_SYS_KEPLER_NOCONV = 4,   /* a Kepler drift did not converge in 50 Newton steps */
+  SWARM_SYS_NONFINITE = 5        /* a position or velocity became NaN or infinite */
+};
+
+/* thread mappings a bin of equal-n systems can run with (Sec. 4.1 work models) */
+enum swarm_mapping {
+  SWARM_MAP_AUTO = 0,            /* autotuner choice (cached per n, integrator, size class) */
+  SWARM_MAP_SYSTEM_PER_LANE = 1, /* one lane integrates a whole system */
+  SWARM_MAP_BODY_PER_LANE = 2,   /* one lane per body, pair terms exchanged by warp shuffles */
+  SWARM_MAP_PLAIN_PER_STEP = 3   /* comparison baseline: one kernel launch per step,
+                                    state re-read from global memory every step */
+};
+
+/* options for swarm_set_option */
+enum swarm_option {
+  SWARM_OPT_MAPPING = 1,        /* enum swarm_mapping, all bins (default AUTO) */
+  SWARM_OPT_N_CORR = 2,         /* Hermite corrector passes, 1..8 (default 2, Sec. 2.2.1) */
+  SWARM_OPT_LOG_INTERVAL = 3,   /* steps between energy/angular-momentum records, 0 = off */
+  SWARM_OPT_LOG_CAPACITY = 4,   /* records kept per system (ring of this size), 0..65536 */
+  SWARM_OPT_STEPS_PER_LAUNCH = 5,/* 0 = whole call in one persistent launch; else launches of
+                                    this many steps, replayed from a captured CUDA graph */
+  SWARM_OPT_SINGLE_LAUNCH = 6,  /* 1 (default): all n-bins share one persistent launch with a
+                                    cost-ordered work list; 0: one launch per bin */
+  SWARM_OPT_CTAS_PER_SM = 7     /* persistent grid size per SM (0 = tuner/default) */
+};
+
+typedef struct swarm_ensemble swarm_ensemble;
+
+/* counters of the last integrate call (exact, counted on the device) */
+typedef struct {
+  int64_t system_steps;       /* steps taken, summed over systems */
+  int64_t pair_evaluations;   /* unique-pair force evaluations (Hermite: 3 per pair per step) */
+  int64_t kepler_iterations;  /* Newton iterations of all Kepler drifts (MVS) */
+  int64_t kernel_launches;    /* kernels launched by the call */
+  double kernel_ms;           /* device time of the call's kernels (CUDA events) */
+} swarm_stats;
+
+/* ------------------------------------------------------------------ ensembles */
+/* Create an ensemble of n_sys systems and upload its initial state (host arrays).
+ * n_body[s] in 2..15; mass > 0 and finite; pos/vel finite; time of every system t0.
+ * cuda_stream: a cudaStream_t to run on (NULL = the legacy default stream).
+ * Returns SWARM_EINVAL for bad sizes/values, SWARM_ENOMEM, SWARM_ECUDA. */
+int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const double *mass, const double *pos,
+                          const double *vel, double t0, void *cuda_stream, swarm_ensemble **out);
+
+/* Stop conditions checked after every step (Algorithm 1 monitor): close encounter when
+ * two planets i, j >= 1 are closer than ce_hill_factor * ((m_i+m_j)/(3 m_0))^(1/3) *
+ * (|x_i-x_0| + |x_j-x_0|)/2, ejection when |x_i - x_0| > eject_radius.  A value <= 0
+ * switches the test off (default: both off).  Non-finite state always stops a system. */
+int swarm_set_stop(swarm_ensemble *ens, double ce_hill_factor, double eject_radius);
+
+int swarm_set_option(swarm_ensemble *ens, int option, int64_t value);
+
+/* Advance every runnable system (status ACTIVE or DONE) from its own time to t_end with
+ * step dt (negative when t_end is earlier).  Step count per system: N = round(D) when
+ * D = (t_end - t)/dt is within 1e-9 of an integer, else ceil(D) with the last step
+ * shortened to land on t_end.  A system that stops keeps the state and time of the
+ * step where it stopped and is never advanced again.  Synchronous: returns after the
+ * device work finished.  SWARM_EINVAL for an unknown integrator, dt = 0 or non-finite. */
+int swarm_integrate(swarm_ensemble *ens, double t_end, int integrator, double dt);
+/* Same, but returns once the work is enqueued on the ensemble's stream. */
+int swarm_integrate_async(swarm_ensemble *ens, double t_end, int integrator, double dt);
+int swarm_synchronize(swarm_ensemble *ens);
+
+/* Replace the state (host arrays in the creation layout; time/status may be NULL to
+ * keep them).  Masses are kept.  Copies in on the stream, then waits. */
+int swarm_set_state(swarm_ensemble *ens, const double *pos, const double *vel, const double *time,
+                    const int32_t *status);
+/* Copy the state out into caller-owned host arrays (any pointer may be NULL). */
+int swarm_query_state(const swarm_ensemble *ens, double *pos, double *vel, double *time, int32_t *status);
+/* Same into caller-owned device arrays, enqueued on the ensemble's stream (no wait). */
+int swarm_query_state_dev(const swarm_ensemble *ens, double *d_pos, double *d_vel, double *d_time,
+                          int32_t *d_status);
+/* Energy (Eq. 6, each pair once) and angular momentum [n_sys][3] of the current state,
+ * computed on the device; host arrays. */
+int swarm_query_diagnostics(const swarm_ensemble *ens, double *energy, double *angmom);
+/* Energy log of one system: records (t, E, Lx, Ly, Lz), oldest first; cap = capacity of
+ * `records` in records; *count gets the number written. */
+int swarm_query_log(const swarm_ensemble *ens, int32_t sys, double *records, int32_t cap, int32_t *count);
+int swarm_query_stats(const swarm_ensemble *ens, swarm_stats *out);
+int32_t swarm_ensemble_size(const swarm_ensemble *ens);
+void swarm_destroy_ensemble(swarm_ensemble *ens);
+
+/* ------------------------------------------------------------------ tuner */
+/* Mapping the autotuner chose for (n, integrator, n_sys); measures on first use. */
+int swarm_tuner_choice(int32_t n, int integrator, int32_t n_sys, void *cuda_stream, int32_t *mapping,
+                       int32_t *ctas_per_sm);
+/* Load / save the tuner cache (text file).  Missing file on load is not an error. */
+int swarm_tuner_load(const char *path);
+int swarm_tuner_save(const char *path);
+
+/* ------------------------------------------------------------------ measurement */
+/* FP64 peak: a DFMA-chain kernel on every SM for about `seconds`; *flops gets
+ * 2 * DFMA/s (the chip's FP64 FLOP/s as measured on this device). */
+int swarm_fp64_peak(double seconds, void *cuda_stream, double *flops);
+
+/* ------------------------------------------------------------------ errors */
+const char *swarm_last_error(void);
+const char *swarm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

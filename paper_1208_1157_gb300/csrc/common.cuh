@@ -1,0 +1,71 @@
+// Shared definitions of the sm_103a path: device layout of an n-bin, kernel parameter
+// blocks, warp helpers and the status codes of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swarm.h"
+
+#define SWARM_MAX_N 15
+#define SWARM_MIN_N 2
+
+namespace swarm {
+
+// One bin = all systems with the same body count n, structure-of-arrays with the system
+// index fastest so that a warp's loads of one field are contiguous:
+//   x[(c * n + b) * S_pad + s], v likewise, m[b * S_pad + s], t[s], status[s].
+struct BinView {
+  int n;          // bodies per system
+  int S;          // systems in the bin
+  int S_pad;      // row pitch (multiple of 32)
+  double *x, *v, *m, *t;
+  int32_t *status;
+  int32_t *gidx;  // ensemble-wide index of bin system s (log buffer rows)
+};
+
+struct StepParams {
+  double t_end, dt;
+  int n_corr;            // Hermite corrector passes
+  int integrator;
+  double ce_factor;      // close-encounter factor in mutual Hill radii (<= 0: off)
+  double eject2;         // squared ejection radius (<= 0: off)
+  int log_interval;      // steps between log records (0: off)
+  int log_cap;           // records per system
+  double *log;           // [n_sys_total][log_cap][5]
+  int32_t *log_count;    // [n_sys_total] records written so far (ring position)
+  unsigned long long *counters;  // [0] system-steps, [1] pair evaluations, [2] Kepler iterations
+  int *work_next;        // dynamic work-list head (persistent multi-bin launch)
+};
+
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Non-finite test on the exponent bits: integer-pipe only, no FP64 instruction.
+__device__ __forceinline__ bool nonfinite(double a) {
+  return (__double2hiint(a) & 0x7ff00000) == 0x7ff00000;
+}
+
+// Per-system step plan of Algorithm 1 with a shortened last step: N = round(D) when
+// D = (t_end - t)/dt is within 1e-9 of an integer, else ceil(D).
+struct StepPlan {
+  long long N;
+  double h_last;
+  int exact;
+};
+__device__ __forceinline__ StepPlan plan_steps(double t, double t_end, double dt) {
+  StepPlan p;
+  double D = (t_end - t) / dt;
+  if (!(D > 1e-9)) {
+    p.N = 0;
+    p.h_last = dt;
+    p.exact = 1;
+    return p;
+  }
+  double Nr = rint(D);
+  p.exact = fabs(D - Nr) <= 1e-9 * fmax(1.0, fabs(D));
+  p.N = p.exact ? (long long)Nr : (long long)ceil(D);
+  p.h_last = p.exact ? dt : t_end - (t + (double)(p.N - 1) * dt);
+  return p;
+}
+
+}  // namespace swarm

@@ -1,0 +1,290 @@
+// Hermite-4 device routines (Sec. 2.2.1, Eqs. 3-4, Algorithm 2) for sm_103a.
+//
+// FP64 is the scarce resource on this chip (2 DFMA per clock per SM, i.e. half a lane
+// per clock on each of the 4 SM sub-partitions; DADD/DMUL issue ~1.2x slower than DFMA;
+// rsqrt(double) ~ 6 DFMA slots).  The routines below therefore
+//  - evaluate every unordered pair once (acceleration and jerk of both bodies),
+//  - keep the corrector in FMA form with step-invariant bases precomputed per step,
+//  - do the monitor's tests with bounds that skip square roots in the common case,
+//  - keep no lane idle that can be avoided.
+#pragma once
+#include "common.cuh"
+
+namespace swarm {
+
+// Coefficients of one step of length h.
+struct HCoef {
+  double h, h2_2, h3_6, hh, h2_12;
+};
+__device__ __forceinline__ HCoef hcoef(double h) {
+  HCoef c;
+  c.h = h;
+  c.h2_2 = 0.5 * h * h;
+  c.h3_6 = c.h2_2 * h * (1.0 / 3.0);
+  c.hh = 0.5 * h;
+  c.h2_12 = h * h * (1.0 / 12.0);
+  return c;
+}
+__device__ __forceinline__ HCoef hsel(bool p, const HCoef &a, const HCoef &b) {
+  HCoef c;
+  c.h = p ? a.h : b.h;
+  c.h2_2 = p ? a.h2_2 : b.h2_2;
+  c.h3_6 = p ? a.h3_6 : b.h3_6;
+  c.hh = p ? a.hh : b.hh;
+  c.h2_12 = p ? a.h2_12 : b.h2_12;
+  return c;
+}
+
+// Geometry of one pair, from body i to body j (Eq. 1 and its time derivative):
+//   dx = x_j - x_i, dv = v_j - v_i, rho = 1/|dx|,
+//   w  = dv - 3 (dx.dv)/|dx|^2 dx   so that   a_i += m_j rho^3 dx,  jerk_i += m_j rho^3 w
+// and the partner receives the opposite terms scaled by m_i.
+__device__ __forceinline__ void pair_geom(const double (&xi)[3], const double (&vi)[3], const double (&xj)[3],
+                                          const double (&vj)[3], double (&dx)[3], double (&w)[3], double &rho3,
+                                          double &r2) {
+  double dv[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    dx[c] = xj[c] - xi[c];
+    dv[c] = vj[c] - vi[c];
+  }
+  r2 = dx[0] * dx[0];
+  r2 = fma(dx[1], dx[1], r2);
+  r2 = fma(dx[2], dx[2], r2);
+  double rv = dx[0] * dv[0];
+  rv = fma(dx[1], dv[1], rv);
+  rv = fma(dx[2], dv[2], rv);
+  double rho = rsqrt(r2);
+  double rho2 = rho * rho;
+  rho3 = rho2 * rho;
+  double cc = -3.0 * (rv * rho2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) w[c] = fma(cc, dx[c], dv[c]);
+}
+
+// ---------------------------------------------------------------- body per lane ("ring")
+// Lanes g*N .. g*N+N-1 of a warp hold the N bodies of system g.  In round r = 1..(N-1)/2
+// lane b evaluates the pair (b, b+r mod N) and hands the partner's share of the pair back
+// to lane b+r by shuffle; for even N a last round r = N/2 has both lanes of each pair take
+// their own share.  Every unordered pair is evaluated exactly once per full round set.
+template <int N>
+struct Ring {
+  static constexpr int G = 32 / N;             // systems per warp
+  static constexpr int RF = (N - 1) / 2;       // full rounds (with reaction)
+  static constexpr bool HALF = (N % 2) == 0;   // extra self-sufficient round
+  static constexpr int RT = RF + (HALF ? 1 : 0);
+};
+
+// MON: also return q2 (squared distance of this body to body 0) and d2[r] (squared
+// distance of this lane's pair in round r) for the monitor.
+template <int N, bool MON>
+__device__ __forceinline__ void ring_accjerk(const double (&x)[3], const double (&v)[3], double m, int b, int base,
+                                             double (&a)[3], double (&jk)[3], double &q2,
+                                             double (&d2)[Ring<N>::RT > 0 ? Ring<N>::RT : 1]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    a[c] = 0.0;
+    jk[c] = 0.0;
+  }
+  q2 = 0.0;
+#pragma unroll
+  for (int r = 1; r <= Ring<N>::RF; r++) {
+    int p = b + r;
+    if (p >= N) p -= N;
+    int q = b - r;
+    if (q < 0) q += N;
+    double xj[3], vj[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      xj[c] = shfl(x[c], base + p);
+      vj[c] = shfl(v[c], base + p);
+    }
+    double mj = shfl(m, base + p);
+    double dx[3], w[3], rho3, r2;
+    pair_geom(x, v, xj, vj, dx, w, rho3, r2);
+    double sj = mj * rho3;
+    double si = m * rho3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      a[c] = fma(sj, dx[c], a[c]);
+      jk[c] = fma(sj, w[c], jk[c]);
+    }
+    // reaction from lane q, which evaluated the pair (q, b)
+    double rdx[3], rw[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      rdx[c] = shfl(dx[c], base + q);
+      rw[c] = shfl(w[c], base + q);
+    }
+    double rs = shfl(si, base + q);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      a[c] = fma(-rs, rdx[c], a[c]);
+      jk[c] = fma(-rs, rw[c], jk[c]);
+    }
+    if (MON) {
+      double rr2 = shfl(r2, base + q);
+      d2[r - 1] = r2;
+      if (p == 0) q2 = r2;
+      if (q == 0) q2 = rr2;
+    }
+  }
+  if (Ring<N>::HALF) {
+    constexpr int r = N / 2;
+    int p = b + r;
+    if (p >= N) p -= N;
+    double xj[3], vj[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      xj[c] = shfl(x[c], base + p);
+      vj[c] = shfl(v[c], base + p);
+    }
+    double mj = shfl(m, base + p);
+    double dx[3], w[3], rho3, r2;
+    pair_geom(x, v, xj, vj, dx, w, rho3, r2);
+    double sj = mj * rho3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      a[c] = fma(sj, dx[c], a[c]);
+      jk[c] = fma(sj, w[c], jk[c]);
+    }
+    if (MON) {
+      d2[Ring<N>::RT - 1] = r2;
+      if (p == 0) q2 = r2;
+    }
+  }
+}
+
+// Energy (Eq. 6, pairs once) and angular momentum of the lane's system, valid in the
+// group's first lane.  Only called at log points.
+template <int N>
+__device__ __forceinline__ void ring_energy(const double (&x)[3], const double (&v)[3], double m, int b, int base,
+                                            double (&out)[4]) {
+  double e = 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double L0 = m * (x[1] * v[2] - x[2] * v[1]);
+  double L1 = m * (x[2] * v[0] - x[0] * v[2]);
+  double L2 = m * (x[0] * v[1] - x[1] * v[0]);
+#pragma unroll
+  for (int r = 1; r <= N / 2; r++) {
+    int p = b + r;
+    if (p >= N) p -= N;
+    double d0 = shfl(x[0], base + p) - x[0];
+    double d1 = shfl(x[1], base + p) - x[1];
+    double d2 = shfl(x[2], base + p) - x[2];
+    double mp = shfl(m, base + p);
+    double pot = m * mp * rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (Ring<N>::HALF && r == N / 2) pot *= 0.5;  // both lanes of the pair count it
+    e -= pot;
+  }
+  double s[4] = {e, L0, L1, L2};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    double tot = s[k];
+#pragma unroll
+    for (int j = 1; j < N; j++) tot += shfl(s[k], base + j);
+    out[k] = tot;
+  }
+  // out[] is the sum over the group only in the group's lane 0 (base + 0 reads base + j);
+  // the other lanes hold partial sums that are not used.
+}
+
+// ---------------------------------------------------------------- system per lane
+// One lane integrates a whole system held in registers; pairs in the order
+// planet-planet first, then star-planet, so every body's star term comes last (Sec. 4.2).
+template <int N>
+__device__ __forceinline__ void spl_accjerk(const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
+                                            double (&a)[N][3], double (&jk)[N][3], double (&q2)[N],
+                                            double (&d2)[N][N]) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      a[i][c] = 0.0;
+      jk[i][c] = 0.0;
+    }
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+      double dx[3], w[3], rho3, r2;
+      pair_geom(x[i], v[i], x[k], v[k], dx, w, rho3, r2);
+      double sk = m[k] * rho3, si = m[i] * rho3;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        a[i][c] = fma(sk, dx[c], a[i][c]);
+        jk[i][c] = fma(sk, w[c], jk[i][c]);
+        a[k][c] = fma(-si, dx[c], a[k][c]);
+        jk[k][c] = fma(-si, w[c], jk[k][c]);
+      }
+      d2[i][k] = r2;
+    }
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    double dx[3], w[3], rho3, r2;
+    pair_geom(x[0], v[0], x[k], v[k], dx, w, rho3, r2);
+    double sk = m[k] * rho3, s0 = m[0] * rho3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      a[0][c] = fma(sk, dx[c], a[0][c]);
+      jk[0][c] = fma(sk, w[c], jk[0][c]);
+      a[k][c] = fma(-s0, dx[c], a[k][c]);
+      jk[k][c] = fma(-s0, w[c], jk[k][c]);
+    }
+    q2[k] = r2;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void spl_energy(const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
+                                           double (&out)[4]) {
+  double e = 0, L0 = 0, L1 = 0, L2 = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    e += 0.5 * m[i] * (v[i][0] * v[i][0] + v[i][1] * v[i][1] + v[i][2] * v[i][2]);
+    L0 += m[i] * (x[i][1] * v[i][2] - x[i][2] * v[i][1]);
+    L1 += m[i] * (x[i][2] * v[i][0] - x[i][0] * v[i][2]);
+    L2 += m[i] * (x[i][0] * v[i][1] - x[i][1] * v[i][0]);
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+      double d0 = x[k][0] - x[i][0], d1 = x[k][1] - x[i][1], d2 = x[k][2] - x[i][2];
+      e -= m[i] * m[k] * rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+  }
+  out[0] = e;
+  out[1] = L0;
+  out[2] = L1;
+  out[3] = L2;
+}
+
+// Close-encounter test of one planet pair: |x_i - x_j| < f k_ij (q_i + q_j)/2 with
+// kc = (f k_ij / 2)^2, k_ij = ((m_i + m_j)/(3 m_0))^(1/3).  The bound
+// (q_i + q_j)^2 <= 2 (q_i^2 + q_j^2) rules most pairs out without a square root.
+__device__ __forceinline__ bool close_encounter(double d2, double kc, double q2i, double q2j) {
+  double t = q2i + q2j;
+  if (d2 < 2.0 * kc * t) {
+    double s = sqrt(q2i) + sqrt(q2j);
+    return d2 < kc * (s * s);
+  }
+  return false;
+}
+
+__device__ __forceinline__ double hill_kc(double ce, double mi, double mj, double m0) {
+  if (!(ce > 0)) return 0.0;
+  double k = cbrt((mi + mj) / (3.0 * m0));
+  double f = 0.5 * ce * k;
+  return f * f;
+}
+
+__device__ __forceinline__ void write_log(const StepParams &P, int gsys, double t, const double (&e)[4]) {
+  int c = P.log_count[gsys];
+  int slot = c % P.log_cap;
+  double *rec = P.log + ((size_t)gsys * P.log_cap + slot) * 5;
+  rec[0] = t;
+  rec[1] = e[0];
+  rec[2] = e[1];
+  rec[3] = e[2];
+  rec[4] = e[3];
+  P.log_count[gsys] = c + 1;
+}
+
+}  // namespace swarm

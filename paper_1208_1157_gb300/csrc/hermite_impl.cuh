@@ -1,0 +1,267 @@
+// Hermite-4 work-unit functions (Algorithm 1 with the Algorithm 2 propagator) in the
+// two thread mappings; instantiated per body count in hermite_units_*.cu.
+#pragma once
+#include "hermite.cuh"
+#include "kernels.h"
+
+namespace swarm {
+
+// ---------------------------------------------------------------- body per lane
+// One work unit = one warp's G = 32/N systems of a bin, integrated for the whole call.
+template <int N>
+__device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+  using R = Ring<N>;
+  constexpr int G = R::G;
+  constexpr int RT = R::RT > 0 ? R::RT : 1;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {  // spare lanes mirror group 0 so every shuffle stays well defined
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int s0 = unit * G;
+  int s = s0 + g;
+  const bool sys_ok = lane_ok && s < B.S;
+  if (s >= B.S) s = s0;
+  const int SP = B.S_pad;
+
+  double x[3], v[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x[c] = B.x[(size_t)(c * N + b) * SP + s];
+    v[c] = B.v[(size_t)(c * N + b) * SP + s];
+  }
+  const double m = B.m[(size_t)b * SP + s];
+  const double t0 = B.t[s];
+  const int st0 = B.status[s];
+  const double m0 = shfl(m, base);
+  const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
+  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
+  const int Ns = runnable ? (int)plan.N : 0;
+  const int Nmax = __reduce_max_sync(FULL, Ns);
+  if (Nmax == 0) {
+    if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+
+  // close-encounter coefficients of this lane's pairs (planet pairs only)
+  double kc[RT];
+#pragma unroll
+  for (int r = 1; r <= RT; r++) {
+    int p = b + r;
+    if (p >= N) p -= N;
+    double mp = shfl(m, base + p);
+    kc[r - 1] = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+  }
+
+  double a0[3], j0[3], q2, d2[RT];
+  ring_accjerk<N, false>(x, v, m, b, base, a0, j0, q2, d2);
+  const HCoef cdt = hcoef(P.dt);
+  const HCoef clast = hcoef(plan.h_last);
+  bool alive = runnable;
+  int steps_done = 0;
+
+  for (int k = 1; k <= Nmax; k++) {
+    const bool active = alive && (k <= Ns);
+    if (!__any_sync(FULL, active)) break;
+    const HCoef C = hsel(k == Ns && !plan.exact, clast, cdt);
+    // Eq. 3 predictor and the step-invariant parts of the corrector
+    double xk[3], vk[3], Xb[3], Vb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      xk[c] = fma(j0[c], C.h3_6, fma(a0[c], C.h2_2, fma(v[c], C.h, x[c])));
+      vk[c] = fma(j0[c], C.h2_2, fma(a0[c], C.h, v[c]));
+      Xb[c] = fma(a0[c], C.h2_12, fma(v[c], C.hh, x[c]));
+      Vb[c] = fma(j0[c], C.h2_12, fma(a0[c], C.hh, v[c]));
+    }
+    // corrector passes (time-symmetric form of Eq. 4)
+    for (int ic = 0; ic < P.n_corr; ic++) {
+      double ak[3], jk[3];
+      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
+        xk[c] = fma(-C.h2_12, ak[c], fma(C.hh, vk[c], Xb[c]));
+      }
+    }
+    // third evaluation: next step's a0, j0 and the monitor's distances
+    double an[3], jn[3];
+    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[c] = xk[c];
+        v[c] = vk[c];
+        a0[c] = an[c];
+        j0[c] = jn[c];
+      }
+      steps_done = k;
+    }
+    // monitor
+    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
+                    nonfinite(v[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+#pragma unroll
+    for (int r = 1; r <= RT; r++) {
+      int p = b + r;
+      if (p >= N) p -= N;
+      double q2p = shfl(q2, base + p);
+      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+    }
+    const unsigned gm = ((1u << N) - 1u) << base;
+    const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
+    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+    const int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    const double tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    if (active && code) {
+      if (sys_ok) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          B.x[(size_t)(c * N + b) * SP + s] = x[c];
+          B.v[(size_t)(c * N + b) * SP + s] = v[c];
+        }
+        if (b == 0) {
+          B.t[s] = tk;
+          B.status[s] = code;
+        }
+      }
+      alive = false;
+    }
+    if (P.log_interval > 0 && (k % P.log_interval) == 0) {
+      double e[4];
+      ring_energy<N>(x, v, m, b, base, e);
+      if (active && !code && b == 0 && sys_ok) write_log(P, B.gidx[s], tk, e);
+    }
+  }
+  if (alive && sys_ok) {
+    if (Ns > 0) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + b) * SP + s] = x[c];
+        B.v[(size_t)(c * N + b) * SP + s] = v[c];
+      }
+    }
+    if (b == 0) {
+      if (Ns > 0) B.t[s] = P.t_end;
+      B.status[s] = SWARM_SYS_DONE;
+    }
+  }
+  if (P.counters && sys_ok && b == 0 && steps_done > 0) {
+    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+    atomicAdd(&P.counters[0], (unsigned long long)steps_done);
+    atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done * (P.n_corr + 1)));
+  }
+}
+
+// ---------------------------------------------------------------- system per lane
+template <int N>
+__device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+  const int s = unit * 32 + (threadIdx.x & 31);
+  if (s >= B.S) return;
+  const int SP = B.S_pad;
+  double x[N][3], v[N][3], m[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    m[i] = B.m[(size_t)i * SP + s];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      x[i][c] = B.x[(size_t)(c * N + i) * SP + s];
+      v[i][c] = B.v[(size_t)(c * N + i) * SP + s];
+    }
+  }
+  const double t0 = B.t[s];
+  if (B.status[s] > SWARM_SYS_DONE) return;
+  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
+  const int Ns = (int)plan.N;
+  if (Ns == 0) {
+    B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+  double kc[N][N];
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
+
+  double a0[N][3], j0[N][3], q2[N], d2[N][N];
+  spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+  const HCoef cdt = hcoef(P.dt);
+  const HCoef clast = hcoef(plan.h_last);
+  int steps_done = 0;
+  int code = 0;
+  double tk = t0;
+  for (int k = 1; k <= Ns; k++) {
+    const HCoef C = (k == Ns && !plan.exact) ? clast : cdt;
+    double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
+        vk[i][c] = fma(j0[i][c], C.h2_2, fma(a0[i][c], C.h, v[i][c]));
+        Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
+        Vb[i][c] = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
+      }
+    for (int ic = 0; ic < P.n_corr; ic++) {
+      double ak[N][3], jk[N][3];
+      spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
+          xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
+        }
+    }
+    spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[i][c] = xk[i][c];
+        v[i][c] = vk[i][c];
+      }
+    steps_done = k;
+    tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    bool nf = false, ej = false, ce = false;
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
+#pragma unroll
+    for (int i = 1; i < N; i++) ej |= (P.eject2 > 0.0) && (q2[i] > P.eject2);
+#pragma unroll
+    for (int i = 1; i < N; i++)
+#pragma unroll
+      for (int k2 = i + 1; k2 < N; k2++)
+        if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+    code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (code) break;
+    if (P.log_interval > 0 && (k % P.log_interval) == 0) {
+      double e[4];
+      spl_energy<N>(x, v, m, e);
+      write_log(P, B.gidx[s], tk, e);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
+      B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
+    }
+  B.t[s] = tk;
+  B.status[s] = code ? code : SWARM_SYS_DONE;
+  if (P.counters) {
+    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+    atomicAdd(&P.counters[0], (unsigned long long)steps_done);
+    atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done * (P.n_corr + 1)));
+  }
+}
+
+}  // namespace swarm

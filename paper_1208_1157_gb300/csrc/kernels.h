@@ -1,0 +1,30 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+#include "common.cuh"
+
+namespace swarm {
+
+// Scratch of the plain one-launch-per-step baseline: a0, j0 between launches and the
+// per-system step plan.
+struct PlainScratch {
+  double *a0, *j0;   // [3][n][S_pad]
+  int *nsteps;       // [S]
+  double *h_last;    // [S]
+  double *t0;        // [S]
+  int *max_steps;    // [1]
+};
+
+cudaError_t launch_hermite_persistent(const BinView *d_bins, const int4 *d_work, int nwork, const StepParams &P,
+                                      int grid, cudaStream_t st);
+int hermite_persistent_max_blocks_per_sm();
+// k = 0: prepare (a0, j0, step plan); k >= 1: step k
+cudaError_t launch_plain(const BinView &B, const StepParams &P, const PlainScratch &W, int k, cudaStream_t st);
+constexpr int kPlainMaxN = 8;
+
+cudaError_t launch_mvs_persistent(const BinView *d_bins, const int4 *d_work, int nwork, const StepParams &P,
+                                  int grid, cudaStream_t st);
+int mvs_persistent_max_blocks_per_sm();
+
+cudaError_t launch_fp64_peak(double *out, long long iters, int grid, int block, cudaStream_t st);
+
+}  // namespace swarm

@@ -1,0 +1,561 @@
+// Mixed-variable symplectic integrator (Sec. 2.2.3, Sec. 4.3.4) on sm_103a, body per lane.
+//
+// Lane b of a group holds body b's canonical coordinates: b = 0 the centre of mass,
+// b >= 1 a planet (democratic heliocentric Q_b = x_b - x_0, u_b = v_b - v_cm; or Jacobi
+// r'_b, v'_b).  Each step runs the paper's sub-steps in order: Cartesian drift half step,
+// kick half step, Kepler drift, kick half step, Cartesian drift half step (DH); kick,
+// Kepler, kick (Jacobi).  The interaction accelerations computed after the Kepler drift
+// are reused by the next step's first kick (Sec. 4.3.4): one force evaluation per step.
+#pragma once
+#include "hermite.cuh"
+#include "kernels.h"
+
+namespace swarm {
+
+// ---------------------------------------------------------------- group collectives
+// All lanes of the warp execute these (full-mask shuffles); each group of N lanes
+// starting at `base` reduces its own values.
+template <int N>
+__device__ __forceinline__ double grp_sum(double val, int b, int base) {
+  // segmented tree: after the loop lane b = 0 of the group holds the sum
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, val, off);
+    val += (b + off < N) ? o : 0.0;
+  }
+  return shfl(val, base);
+}
+
+// exclusive prefix sum over the group (lane b gets the sum over lanes 0..b-1)
+template <int N>
+__device__ __forceinline__ double grp_scan_excl(double val, int b) {
+  double inc = val;
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_up_sync(0xffffffffu, inc, off);
+    inc += (b >= off) ? o : 0.0;
+  }
+  double ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  return b > 0 ? ex : 0.0;
+}
+
+// exclusive suffix sum (lane b gets the sum over lanes b+1..N-1)
+template <int N>
+__device__ __forceinline__ double grp_suffix_excl(double val, int b) {
+  double inc = val;
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, inc, off);
+    inc += (b + off < N) ? o : 0.0;
+  }
+  double ex = __shfl_down_sync(0xffffffffu, inc, 1);
+  return b + 1 < N ? ex : 0.0;
+}
+
+// ---------------------------------------------------------------- acceleration ring
+// Acceleration only (Eq. 1), over M members at lanes base+OFF .. base+OFF+M-1; member j.
+// Lanes outside the members (the centre-of-mass lane in DH) mirror member 0 and their
+// results are discarded.
+template <int M>
+struct ARing {
+  static constexpr int RF = (M - 1) / 2;
+  static constexpr bool HALF = (M % 2) == 0 && M > 0;
+  static constexpr int RT = RF + (HALF ? 1 : 0);
+  static constexpr int RTA = RT > 0 ? RT : 1;
+};
+
+template <int M, int OFF>
+__device__ __forceinline__ void ring_acc(const double (&x)[3], double m, int j, int base, double (&a)[3],
+                                         double (&d2)[ARing<M>::RTA]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) a[c] = 0.0;
+#pragma unroll
+  for (int r = 1; r <= ARing<M>::RF; r++) {
+    int p = j + r;
+    if (p >= M) p -= M;
+    int q = j - r;
+    if (q < 0) q += M;
+    double dx[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], base + OFF + p) - x[c];
+    double mp = shfl(m, base + OFF + p);
+    double r2 = dx[0] * dx[0];
+    r2 = fma(dx[1], dx[1], r2);
+    r2 = fma(dx[2], dx[2], r2);
+    double rho = rsqrt(r2);
+    double rho3 = rho * rho * rho;
+    double sp = mp * rho3, si = m * rho3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
+    double rdx[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) rdx[c] = shfl(dx[c], base + OFF + q);
+    double rs = shfl(si, base + OFF + q);
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = fma(-rs, rdx[c], a[c]);
+    d2[r - 1] = r2;
+  }
+  if (ARing<M>::HALF) {
+    constexpr int r = M / 2;
+    int p = j + r;
+    if (p >= M) p -= M;
+    double dx[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], base + OFF + p) - x[c];
+    double mp = shfl(m, base + OFF + p);
+    double r2 = dx[0] * dx[0];
+    r2 = fma(dx[1], dx[1], r2);
+    r2 = fma(dx[2], dx[2], r2);
+    double rho = rsqrt(r2);
+    double sp = mp * (rho * rho * rho);
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
+    d2[ARing<M>::RT - 1] = r2;
+  }
+}
+
+// ---------------------------------------------------------------- Stumpff and Kepler
+// c2(z), c3(z) by their power series on |z| <= 0.1, reaching larger |z| by quartering
+// the argument and the doubling relations c0(4z) = 2 c0^2 - 1, c1(4z) = c0 c1,
+// c2(4z) = c1^2 / 2, c3(4z) = (c2 + c0 c3) / 4 (Danby 1988, Sec. 6.9).
+__device__ __forceinline__ void stumpff23(double z, double &c2, double &c3) {
+  int k = 0;
+  while (fabs(z) > 0.1 && k < 40) {
+    z *= 0.25;
+    k++;
+  }
+  // Horner forms of sum (-z)^i/(2i+2)! (i <= 7) and sum (-z)^i/(2i+3)! (i <= 7)
+  c2 = fma(z, 1.0 / 20922789888000.0, -1.0 / 87178291200.0);
+  c2 = fma(z, c2, 1.0 / 479001600.0);
+  c2 = fma(z, c2, -1.0 / 3628800.0);
+  c2 = fma(z, c2, 1.0 / 40320.0);
+  c2 = fma(z, c2, -1.0 / 720.0);
+  c2 = fma(z, c2, 1.0 / 24.0);
+  c2 = fma(z, c2, -0.5);
+  c2 = -c2;
+  c3 = fma(z, -1.0 / 355687428096000.0, 1.0 / 1307674368000.0);
+  c3 = fma(z, c3, -1.0 / 6227020800.0);
+  c3 = fma(z, c3, 1.0 / 39916800.0);
+  c3 = fma(z, c3, -1.0 / 362880.0);
+  c3 = fma(z, c3, 1.0 / 5040.0);
+  c3 = fma(z, c3, -1.0 / 120.0);
+  c3 = fma(z, c3, 1.0 / 6.0);
+  if (k) {
+    double c1 = fma(-z, c3, 1.0);
+    double c0 = fma(-z, c2, 1.0);
+    for (int i = 0; i < k; i++) {
+      c3 = 0.25 * fma(c0, c3, c2);
+      c2 = 0.5 * c1 * c1;
+      c1 = c0 * c1;
+      c0 = fma(2.0 * c0, c0, -1.0);
+    }
+  }
+}
+
+struct KepConst {
+  double mu, smu, smuinv, muinv;
+};
+__device__ __forceinline__ KepConst kep_const(double mu) {
+  KepConst k;
+  k.mu = mu;
+  k.smu = sqrt(mu);
+  k.smuinv = 1.0 / k.smu;
+  k.muinv = 1.0 / mu;
+  return k;
+}
+
+// Starting guesses of Vallado, "Fundamentals of Astrodynamics and Applications",
+// Algorithm 8 (elliptic, hyperbolic, parabolic).
+static __device__ __noinline__ double chi_guess(const KepConst &K, const double (&r)[3], const double (&v)[3], double r0, double sig0,
+                            double alpha, double h) {
+  if (alpha > 1e-6) return K.smu * alpha * h;
+  if (alpha < -1e-6) {
+    double a = 1.0 / alpha;
+    double sg = h >= 0 ? 1.0 : -1.0;
+    double arg = (-2.0 * K.mu * alpha * h) / (sig0 + sg * sqrt(-K.mu * a) * (1.0 - r0 * alpha));
+    return arg > 0 ? sg * sqrt(-a) * log(arg) : K.smu * h / r0;
+  }
+  double hx = r[1] * v[2] - r[2] * v[1], hy = r[2] * v[0] - r[0] * v[2], hz = r[0] * v[1] - r[1] * v[0];
+  double p = (hx * hx + hy * hy + hz * hz) * K.muinv;
+  double s = 0.5 * atan(1.0 / (3.0 * sqrt(K.mu / (p * p * p)) * h));
+  double w = atan(cbrt(tan(s)));
+  return sqrt(p) * 2.0 / tan(2.0 * w);
+}
+
+// Universal-variable Kepler drift of (r, v) by h: Newton on
+//   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
+// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|); then the Lagrange f, g,
+// fdot, gdot.  `chi` carries the previous step's solution as the starting point (warm
+// start; `have_chi` false on the first step of a call).  Executed by every lane of the
+// warp; lanes with `on` false do not change their state.  Returns false on
+// non-convergence in 50 iterations.
+static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, double (&r)[3], double (&v)[3], double h, double &chi,
+                             bool have_chi, int &iters) {
+  const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  const double rinv0 = rsqrt(r2);
+  const double r0 = r2 * rinv0;
+  const double sig0 = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double alpha = fma(-v2, K.muinv, 2.0 * rinv0);
+  const double s0 = sig0 * K.smuinv;
+  const double beta = fma(-alpha, r0, 1.0);
+  const double target = K.smu * h;
+  double x = chi;
+  if (on && !have_chi) x = chi_guess(K, r, v, r0, sig0, alpha, h);
+  bool done = !on;
+  int it = 0;
+  for (int i = 0; i < 50; i++) {
+    if (__all_sync(0xffffffffu, done)) break;
+    if (!done) {
+      double x2 = x * x;
+      double z = alpha * x2;
+      double c2, c3;
+      stumpff23(z, c2, c3);
+      double x3 = x2 * x;
+      double F = fma(s0 * x2, c2, fma(beta * x3, c3, fma(r0, x, -target)));
+      double dF = fma(s0 * x, fma(-z, c3, 1.0), fma(beta * x2, c2, r0));
+      double dx = F / dF;
+      x -= dx;
+      it++;
+      if (fabs(dx) <= 1e-14 * fmax(1.0, fabs(x))) done = true;
+    }
+  }
+  iters = it;
+  if (!on) return true;
+  if (!done) return false;
+  const double x2 = x * x;
+  const double z = alpha * x2;
+  double c2, c3;
+  stumpff23(z, c2, c3);
+  const double x2c2 = x2 * c2;
+  const double x3c3 = x2 * x * c3;
+  const double f = fma(-x2c2, rinv0, 1.0);
+  const double g = fma(-x3c3, K.smuinv, h);
+  double rn[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], g * v[c]);
+  const double rr = sqrt(rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2]);
+  const double rinv = 1.0 / rr;
+  const double fd = K.smu * x * fma(z, c3, -1.0) * (rinv0 * rinv);
+  const double gd = fma(-x2c2, rinv, 1.0);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    v[c] = fma(fd, r[c], gd * v[c]);
+    r[c] = rn[c];
+  }
+  chi = x;
+  return true;
+}
+
+// ---------------------------------------------------------------- coordinate maps
+// inertial (x, v) of the lane's body -> DH (q, u); all lanes execute
+template <int N>
+__device__ __forceinline__ void to_dh(const double (&x)[3], const double (&v)[3], double m, double Minv, int b,
+                                      int base, double (&q)[3], double (&u)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double X = grp_sum<N>(m * x[c], b, base) * Minv;
+    double V = grp_sum<N>(m * v[c], b, base) * Minv;
+    double x0 = shfl(x[c], base);
+    q[c] = b == 0 ? X : x[c] - x0;
+    u[c] = b == 0 ? V : v[c] - V;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void from_dh(const double (&q)[3], const double (&u)[3], double m, double m0,
+                                        double Minv, int b, int base, double (&x)[3], double (&v)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double sq = grp_sum<N>(b == 0 ? 0.0 : m * q[c], b, base);
+    double su = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
+    double X = shfl(q[c], base), V = shfl(u[c], base);
+    double x0 = X - sq * Minv;
+    double v0 = V - su / m0;
+    x[c] = b == 0 ? x0 : q[c] + x0;
+    v[c] = b == 0 ? v0 : u[c] + V;
+  }
+}
+
+// Jacobi: r'_b = x_b - (sum_{k<b} m_k x_k)/eta_{b-1}; r'_0 = centre of mass
+template <int N>
+__device__ __forceinline__ void to_jacobi(const double (&x)[3], const double (&v)[3], double m, double Minv,
+                                          double eta_prev_inv, int b, int base, double (&q)[3], double (&u)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double px = grp_scan_excl<N>(m * x[c], b);
+    double pv = grp_scan_excl<N>(m * v[c], b);
+    double X = grp_sum<N>(m * x[c], b, base) * Minv;
+    double V = grp_sum<N>(m * v[c], b, base) * Minv;
+    q[c] = b == 0 ? X : x[c] - px * eta_prev_inv;
+    u[c] = b == 0 ? V : v[c] - pv * eta_prev_inv;
+  }
+}
+
+// x_b = r'_b + CoM - sum_{k>=b} w_k r'_k (b >= 1), x_0 = CoM - sum_{k>=1} w_k r'_k,
+// w_k = m_k / eta_k
+template <int N>
+__device__ __forceinline__ void from_jacobi(const double (&q)[3], const double (&u)[3], double w, int b, int base,
+                                            double (&x)[3], double (&v)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double cq = b == 0 ? 0.0 : w * q[c];
+    double cu = b == 0 ? 0.0 : w * u[c];
+    double sq = grp_suffix_excl<N>(cq, b) + cq;  // inclusive suffix from b
+    double su = grp_suffix_excl<N>(cu, b) + cu;
+    double s1q = shfl(sq, base + 1), s1u = shfl(su, base + 1);
+    double X = shfl(q[c], base), V = shfl(u[c], base);
+    x[c] = b == 0 ? X - s1q : q[c] + X - sq;
+    v[c] = b == 0 ? V - s1u : u[c] + V - su;
+  }
+}
+
+// heliocentric positions from Jacobi ones: Q_b = r'_b + sum_{1<=k<b} w_k r'_k, Q_0 = 0
+template <int N>
+__device__ __forceinline__ void jacobi_helio(const double (&q)[3], double w, int b, double (&Q)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double pre = grp_scan_excl<N>(b == 0 ? 0.0 : w * q[c], b);
+    Q[c] = b == 0 ? 0.0 : q[c] + pre;
+  }
+}
+
+// Interaction acceleration.  DH: planet-planet terms (Sec. 2.2.3).  Jacobi: Jacobi
+// components of all pair accelerations plus mu_b r'_b/|r'_b|^3.
+template <int N, bool JAC>
+__device__ __forceinline__ void mvs_acc(const double (&q)[3], double m, double w, double eta_prev_inv, double mu,
+                                        int b, int base, double (&acc)[3], double (&Q)[3],
+                                        double (&d2)[ARing<(JAC ? N : N - 1)>::RTA]) {
+  if constexpr (!JAC) {
+    ring_acc<N - 1, 1>(q, m, b == 0 ? 0 : b - 1, base, acc, d2);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      if (b == 0) acc[c] = 0.0;
+      Q[c] = q[c];
+    }
+  } else {
+    jacobi_helio<N>(q, w, b, Q);
+    double a[3];
+    ring_acc<N, 0>(Q, m, b, base, a, d2);
+    const double r2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    const double rho = rsqrt(r2);
+    const double k = mu * rho * rho * rho;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double pre = grp_scan_excl<N>(m * a[c], b);
+      acc[c] = b == 0 ? 0.0 : fma(-pre, eta_prev_inv, fma(k, q[c], a[c]));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- one work unit
+template <int N, bool JAC>
+__device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P, int unit) {
+  constexpr int G = 32 / N;
+  constexpr int MR = JAC ? N : N - 1;  // members of the acceleration ring
+  constexpr int RTA = ARing<MR>::RTA;
+  constexpr int RT = ARing<MR>::RT;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int s0 = unit * G;
+  int s = s0 + g;
+  const bool sys_ok = lane_ok && s < B.S;
+  if (s >= B.S) s = s0;
+  const int SP = B.S_pad;
+
+  double x[3], v[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x[c] = B.x[(size_t)(c * N + b) * SP + s];
+    v[c] = B.v[(size_t)(c * N + b) * SP + s];
+  }
+  const double m = B.m[(size_t)b * SP + s];
+  const double t0 = B.t[s];
+  const int st0 = B.status[s];
+  const double m0 = shfl(m, base);
+  const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
+  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
+  const int Ns = runnable ? (int)plan.N : 0;
+  const int Nmax = __reduce_max_sync(FULL, Ns);
+  if (Nmax == 0) {
+    if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+
+  // masses: M, eta_b (prefix), 1/eta_{b-1}, w_b = m_b/eta_b, Kepler parameter
+  const double Mtot = grp_sum<N>(m, b, base);
+  const double Minv = 1.0 / Mtot;
+  const double eta = grp_scan_excl<N>(m, b) + m;
+  const double eta_prev = eta - m;
+  const double eta_prev_inv = b == 0 ? 0.0 : 1.0 / eta_prev;
+  const double w = m / eta;
+  const double mu = JAC ? (b == 0 ? m0 : m0 * eta * eta_prev_inv) : m0;
+  const KepConst K = kep_const(mu);
+  const double m0inv = 1.0 / m0;
+
+  // close-encounter coefficients of this lane's ring pairs (planet pairs only)
+  double kc[RTA];
+  {
+    const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
+#pragma unroll
+    for (int r = 1; r <= RTA; r++) {
+      int p = jm + r;
+      if (p >= MR) p -= MR;
+      const int pl = JAC ? p : p + 1;  // body index of the partner
+      double mp = shfl(m, base + (JAC ? 0 : 1) + p);
+      kc[r - 1] = (b != 0 && pl != 0 && r <= RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+    }
+  }
+
+  double q[3], u[3];
+  if (JAC) to_jacobi<N>(x, v, m, Minv, eta_prev_inv, b, base, q, u);
+  else to_dh<N>(x, v, m, Minv, b, base, q, u);
+  double acc[3], Q[3], d2[RTA];
+#pragma unroll
+  for (int r = 0; r < RTA; r++) d2[r] = 0.0;
+  mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+
+  bool alive = runnable;
+  int steps_done = 0;
+  double chi = 0.0;
+  bool have_chi = false;
+  unsigned long long kep_iters = 0;
+
+  for (int k = 1; k <= Nmax; k++) {
+    const bool active = alive && (k <= Ns);
+    if (!__any_sync(FULL, active)) break;
+    const double h = (k == Ns && !plan.exact) ? plan.h_last : P.dt;
+    const double hh = 0.5 * h;
+    double qs[3] = {q[0], q[1], q[2]}, us[3] = {u[0], u[1], u[2]}, as[3] = {acc[0], acc[1], acc[2]};
+    if (!JAC) {
+      // Cartesian drift half step: CoM by v_cm, planets by the star's reflex sum m_j u_j / m0
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+        if (b == 0) q[c] = fma(h, u[c], q[c]);  // centre of mass drifts with its velocity
+    }
+    // kick half step with the cached accelerations
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
+    // Keplerian drift of every planet
+    int its = 0;
+    bool ok = kepler_drift(active && b != 0, K, q, u, h, chi, have_chi, its);
+    have_chi = true;
+    kep_iters += its;
+    // accelerations at the new positions, reused by the next step's first kick
+    mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
+    if (!JAC) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        Q[c] = q[c];
+      }
+    }
+    if (!active) {  // stopped or finished groups keep their state
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        q[c] = qs[c];
+        u[c] = us[c];
+        acc[c] = as[c];
+      }
+    } else {
+      steps_done = k;
+    }
+    // monitor on the heliocentric positions at the end of the step
+    const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    const bool nf = nonfinite(q[0]) | nonfinite(q[1]) | nonfinite(q[2]) | nonfinite(u[0]) | nonfinite(u[1]) |
+                    nonfinite(u[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+    {
+      const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
+#pragma unroll
+      for (int r = 1; r <= RTA; r++) {
+        int p = jm + r;
+        if (p >= MR) p -= MR;
+        double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
+        if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      }
+    }
+    const unsigned gm = ((1u << N) - 1u) << base;
+    const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
+    const unsigned bkn = __ballot_sync(FULL, active && !ok) & gm;
+    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+    const int code = bkn ? SWARM_SYS_KEPLER_NOCONV
+                         : bnf ? SWARM_SYS_NONFINITE
+                               : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    const double tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    const bool want_log = P.log_interval > 0 && (k % P.log_interval) == 0;
+    if (__any_sync(FULL, active && code != 0) || want_log) {
+      double xo[3], vo[3];
+      if (JAC) from_jacobi<N>(q, u, w, b, base, xo, vo);
+      else from_dh<N>(q, u, m, m0, Minv, b, base, xo, vo);
+      if (active && code) {
+        if (sys_ok) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            B.x[(size_t)(c * N + b) * SP + s] = xo[c];
+            B.v[(size_t)(c * N + b) * SP + s] = vo[c];
+          }
+          if (b == 0) {
+            B.t[s] = tk;
+            B.status[s] = code;
+          }
+        }
+        alive = false;
+      }
+      if (want_log) {
+        double e[4];
+        ring_energy<N>(xo, vo, m, b, base, e);
+        if (active && !code && b == 0 && sys_ok) write_log(P, B.gidx[s], tk, e);
+      }
+    }
+  }
+  // back to inertial coordinates for the groups that ran to t_end
+  {
+    double xo[3], vo[3];
+    if (JAC) from_jacobi<N>(q, u, w, b, base, xo, vo);
+    else from_dh<N>(q, u, m, m0, Minv, b, base, xo, vo);
+    if (alive && sys_ok) {
+      if (Ns > 0) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          B.x[(size_t)(c * N + b) * SP + s] = xo[c];
+          B.v[(size_t)(c * N + b) * SP + s] = vo[c];
+        }
+      }
+      if (b == 0) {
+        if (Ns > 0) B.t[s] = P.t_end;
+        B.status[s] = SWARM_SYS_DONE;
+      }
+    }
+  }
+  if (P.counters) {
+    unsigned long long its = sys_ok ? kep_iters : 0ull;
+    if (its) atomicAdd(&P.counters[2], its);
+    if (sys_ok && b == 0 && steps_done > 0) {
+      constexpr unsigned long long NP = JAC ? (unsigned long long)N * (N - 1) / 2
+                                            : (unsigned long long)(N - 1) * (N - 2) / 2;
+      atomicAdd(&P.counters[0], (unsigned long long)steps_done);
+      atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done));
+    }
+  }
+}
+
+}  // namespace swarm

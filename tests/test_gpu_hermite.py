@@ -1,0 +1,152 @@
+"""GPU parity of the Hermite-4 path (C ABI -> sm_103a kernels) against the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import TWO_PI, assert_parity, oracle_sensitivity, per_system_errors, run_gpu, run_oracle
+from paper_1208_1157_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+DT = TWO_PI * 1e-3
+MAPS = {"body_per_lane": 2, "system_per_lane": 1, "plain_per_step": 3, "auto": 0}
+
+
+@pytest.fixture(scope="module")
+def c1():
+    # 1024 star + 2 planet systems (seed 1), 1000 steps of dt = 1e-3 inner periods
+    ens = ics.three_body(1024, seed=1)
+    sens = oracle_sensitivity(ens, 1000 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    return ens, run_oracle(ens, 1000 * DT, O.HERMITE, DT, ce=3.0, ej=100.0), sens
+
+
+@pytest.mark.parametrize("mapping", list(MAPS))
+def test_three_body_parity_1000_steps(c1, mapping):
+    ens, o, sens = c1
+    g = run_gpu(ens, 1000 * DT, 1, DT, mapping=MAPS[mapping], ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens)
+    assert g["stats"]["system_steps"] == int(np.sum(np.round(o["time"] / DT)))
+
+
+def test_ragged_parity_all_body_counts():
+    # n = 2..15 mixed, Hill-spaced, several warps per bin and ragged tails
+    ens = ics.concat(ics.ragged(520, seed=3), ics.subset(ics.two_body(1.3, 0.2), [0]))
+    o = run_oracle(ens, 200 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, 200 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    for single in (1, 0):
+        g = run_gpu(ens, 200 * DT, 1, DT, mapping=2, ce=3.0, ej=100.0, single_launch=single)
+        assert_parity(ens, g, o, sens=sens, steps=200)
+
+
+def test_shortened_last_step_and_continuation():
+    ens = ics.three_body(100, seed=5)
+    t1 = 123.4567 * DT  # not a multiple of dt: the last step is shortened
+    o = run_oracle(ens, t1, O.HERMITE, DT)
+    g = run_gpu(ens, t1, 1, DT, mapping=2)
+    assert_parity(ens, g, o)
+    assert np.all(g["time"] == t1)
+    # two calls to 2T equal one call (same steps, a0/j0 recomputed from the state)
+    from paper_1208_1157_gb300 import swarm as S
+    with S.Ensemble(ens) as e:
+        e.integrate(300 * DT, S.HERMITE4, DT)
+        e.integrate(600 * DT, S.HERMITE4, DT)
+        two = e.state()
+    one = run_gpu(ens, 600 * DT, 1, DT)
+    ex, ev = per_system_errors(ens, two, one)
+    assert ex.max() <= 1e-14 and ev.max() <= 1e-14
+
+
+def test_time_reversal_on_gpu():
+    ens = ics.three_body(64, seed=7)
+    from paper_1208_1157_gb300 import swarm as S
+    with S.Ensemble(ens) as e:
+        e.set_option(S.OPT_N_CORR, 8)
+        e.integrate(200 * DT, S.HERMITE4, DT)
+        e.integrate(0.0, S.HERMITE4, -DT)
+        back = e.state()
+    ex, ev = per_system_errors(ens, back, ens)
+    assert ex.max() <= 1e-13 and ev.max() <= 1e-13
+    assert np.all(back["time"] == 0.0)
+
+
+def test_stop_conditions_match_oracle():
+    ens = ics.three_body(64, seed=8)
+    # system 3: planet 2 on an escape orbit from 95 AU; system 9: planets nearly touching
+    ens["pos"][3 * 3 + 2] = [95.0, 0.0, 0.0]
+    ens["vel"][3 * 3 + 2] = [1.5, 0.0, 0.0]
+    ens["pos"][3 * 9 + 2] = ens["pos"][3 * 9 + 1] + np.array([0.05, 0.0, 0.0])
+    ens["vel"][3 * 9 + 2] = ens["vel"][3 * 9 + 1]
+    o = run_oracle(ens, 3000 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    assert o["status"][3] == O.EJECTED and o["status"][9] == O.CLOSE_ENCOUNTER
+    for mapping in (2, 1, 3):
+        g = run_gpu(ens, 3000 * DT, 1, DT, mapping=mapping, ce=3.0, ej=100.0)
+        assert_parity(ens, g, o, check_energy=False)
+
+
+def test_stopped_systems_are_not_advanced_and_zero_step_call():
+    ens = ics.three_body(40, seed=9)
+    st = np.zeros(40, dtype=np.int32)
+    st[[1, 7]] = [O.EJECTED, O.CLOSE_ENCOUNTER]
+    tm = np.zeros(40)
+    o = run_oracle(ens, 50 * DT, O.HERMITE, DT, time=tm, status=st)
+    g = run_gpu(ens, 50 * DT, 1, DT, time=tm, status=st)
+    assert_parity(ens, g, o)
+    assert np.array_equal(g["pos"][3:6], ens["pos"][3:6])
+    # t_end equal to the current time: no step, status DONE, state unchanged
+    g0 = run_gpu(ens, 0.0, 1, DT)
+    assert np.all(g0["status"] == O.DONE) and np.array_equal(g0["pos"], ens["pos"])
+
+
+def test_energy_log_matches_oracle():
+    ens = ics.three_body(48, seed=10)
+    o = run_oracle(ens, 1000 * DT, O.HERMITE, DT, log_interval=100, log_cap=20)
+    for mapping in (2, 1, 3):
+        g = run_gpu(ens, 1000 * DT, 1, DT, mapping=mapping, log_interval=100, log_cap=20)
+        for s in range(48):
+            lg, lo = g["logs"][s], o["log"][s, : o["log_count"][s]]
+            assert lg.shape == lo.shape == (10, 5)
+            np.testing.assert_allclose(lg[:, 0], lo[:, 0], rtol=1e-14)
+            np.testing.assert_allclose(lg[:, 1], lo[:, 1], rtol=1e-11)
+            np.testing.assert_allclose(lg[:, 2:], lo[:, 2:], rtol=1e-11, atol=1e-16)
+
+
+def test_diagnostics_match_oracle():
+    ens = ics.ragged(200, seed=11)
+    g = run_gpu(ens, 10 * DT, 1, DT)
+    offs = np.concatenate([[0], np.cumsum(ens["n_body"])])
+    for s in range(200):
+        sl = slice(offs[s], offs[s + 1])
+        E, L = O.energy(ens["mass"][sl], g["pos"][sl], g["vel"][sl])
+        assert g["energy"][s] == pytest.approx(E, rel=1e-13)
+        np.testing.assert_allclose(g["angmom"][s], L, rtol=1e-12, atol=1e-18)
+
+
+def test_paper_shaped_ensemble_full_size_sampled():
+    # 131072 x 3 bodies, 10^4 steps: the benchmark's configuration; 32 sampled systems
+    ens = ics.three_body(131072, seed=2)
+    g = run_gpu(ens, 10000 * DT, 1, DT, ce=3.0, ej=100.0)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(131072, 32, replace=False))
+    sub = ics.subset(ens, idx)
+    o = run_oracle(sub, 10000 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, 10000 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    gs = {"pos": g["pos"].reshape(-1, 3, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 3, 3)[idx].reshape(-1, 3),
+          "time": g["time"][idx], "status": g["status"][idx]}
+    # 10^4 steps: the 1000-step bar, scaled by the step count
+    assert_parity(sub, gs, o, tol=1e-9, sens=sens, steps=10000)
+    assert g["stats"]["system_steps"] > 0.99 * 131072 * 10000
+
+
+def test_ragged_full_size_sampled():
+    ens = ics.ragged(65536, seed=3)
+    g = run_gpu(ens, 10 * DT, 1, DT, mapping=0)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(65536, 40, replace=False))
+    sub = ics.subset(ens, idx)
+    o = run_oracle(sub, 10 * DT, O.HERMITE, DT)
+    offs = np.concatenate([[0], np.cumsum(ens["n_body"])])
+    rows = np.concatenate([np.arange(offs[s], offs[s + 1]) for s in idx])
+    gs = {"pos": g["pos"][rows], "vel": g["vel"][rows], "time": g["time"][idx], "status": g["status"][idx]}
+    assert_parity(sub, gs, o)

@@ -1,0 +1,72 @@
+"""GPU parity of the MVS path (democratic heliocentric and Jacobi) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import closed_forms as cf
+import oracle as O
+from gpu_util import TWO_PI, assert_parity, oracle_sensitivity, run_gpu, run_oracle
+from paper_1208_1157_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+DT = TWO_PI / 20  # 1/20 of the inner period
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_compact_eight_body_parity_1000_steps(kind):
+    ens = ics.mvs_compact(256, seed=4)
+    o = run_oracle(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens)
+    # warm-started Newton: between one and (on average) a handful of iterations per solve
+    solves = 7 * int(np.sum(np.round(o["time"] / DT)))
+    assert solves <= g["stats"]["kepler_iterations"] <= 6 * solves
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_ragged_mvs_parity(kind):
+    ens = ics.ragged(300, seed=12)
+    o = run_oracle(ens, 300 * DT, kind, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, 300 * DT, kind, DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, 300 * DT, kind, DT, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens, steps=300)
+
+
+def test_jacobi_two_body_exact():
+    m0, m1 = 1.0, 1e-3
+    s = ics.two_body(1.0, 0.3, m0, m1, E0=0.2)
+    ens = ics.concat(*[s] * 40)
+    g = run_gpu(ens, 7.3, O.MVS_JACOBI, 7.3 / 3)
+    rr, vr = cf.elliptic_at(m0 + m1, 1.0, 0.3, 0.2, 7.3)
+    for k in range(40):
+        x, v = g["pos"][2 * k:2 * k + 2], g["vel"][2 * k:2 * k + 2]
+        assert np.max(np.abs(x[1] - x[0] - rr)) <= 1e-12 * np.max(np.abs(rr))
+        assert np.max(np.abs(v[1] - v[0] - vr)) <= 1e-12 * np.max(np.abs(vr))
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_mvs_shortened_last_step_and_log(kind):
+    ens = ics.mvs_compact(64, seed=13)
+    t1 = 77.3 * DT
+    o = run_oracle(ens, t1, kind, DT, log_interval=10, log_cap=10)
+    g = run_gpu(ens, t1, kind, DT, log_interval=10, log_cap=10)
+    assert_parity(ens, g, o)
+    for s in range(64):
+        lo = o["log"][s, : o["log_count"][s]]
+        np.testing.assert_allclose(g["logs"][s][:, 1], lo[:, 1], rtol=1e-11)
+
+
+def test_mvs_full_size_sampled():
+    # 16384 x 8 bodies in the benchmark's launch configuration; 1000 steps, 24 samples
+    ens = ics.mvs_compact(16384, seed=4)
+    g = run_gpu(ens, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    idx = np.sort(np.random.default_rng(2).choice(16384, 24, replace=False))
+    sub = ics.subset(ens, idx)
+    o = run_oracle(sub, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    gs = {"pos": g["pos"].reshape(-1, 8, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 8, 3)[idx].reshape(-1, 3),
+          "time": g["time"][idx], "status": g["status"][idx]}
+    assert_parity(sub, gs, o, sens=sens)
