@@ -152,6 +152,39 @@ int swarm_tuner_save(const char *path);
  * 2 * DFMA/s (the chip's FP64 FLOP/s as measured on this device). */
 int swarm_fp64_peak(double seconds, void *cuda_stream, double *flops);
 
+/* ------------------------------------------------------------------ allocation-free variant */
+/* The paper has no counterpart of this entry point.
+ *
+ * For callers that cannot allocate device memory: code that runs inside another
+ * framework's memory pool or under a fixed device-memory budget where a cudaMalloc
+ * would fail or evict the host application's own buffers, real-time loops that must
+ * not take the implicit device synchronization of cudaMalloc/cudaFree, and plugins that
+ * may only touch buffers handed to them.  It runs the same persistent Hermite-4 kernel
+ * as swarm_integrate (two corrector passes, the monitor of swarm_set_stop, no energy
+ * log, no statistics) on one bin of equal-n systems that the caller keeps in its own
+ * device memory, and allocates nothing: its working storage (bin descriptor, work list,
+ * work counter) is a fixed 1 MiB array in device global memory that every GPU loading
+ * this library holds until the process exits.
+ *
+ * Layout (all device pointers, caller-owned, in the library's bin layout, system index
+ * fastest): x and v [3][n][s_pad] with element (c, b, s) at (c*n + b)*s_pad + s, m
+ * [n][s_pad], t [n_sys], status [n_sys] (enum swarm_sys_status; stopped systems are left
+ * alone).  x, v, t, status are updated in place; m is read.  n in 2..15, 1 <= n_sys <=
+ * s_pad.  Mapping: a system per lane for n <= 3, a body per lane otherwise (fixed; the
+ * autotuner is not used because it allocates).  Limit: at most 65520 work units, i.e.
+ * 65520*32 systems for n <= 3 and 65520*floor(32/n) systems otherwise; larger ensembles
+ * get SWARM_EINVAL with a message in swarm_last_error().
+ *
+ * The call enqueues its kernels on cuda_stream and returns; read the results after
+ * synchronizing that stream.  The first call on a device looks up the device address
+ * of the array (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and each call resets its
+ * counter, so calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race: serialize them. */
+int swarm_hermite_integrate_noalloc(int32_t n, int32_t n_sys, int32_t s_pad, double *d_x, double *d_v,
+                                    const double *d_m, double *d_t, int32_t *d_status, double t_end, double dt,
+                                    double ce_hill_factor, double eject_radius, void *cuda_stream);
+
 /* ------------------------------------------------------------------ errors */
 const char *swarm_last_error(void);
 const char *swarm_version(void);

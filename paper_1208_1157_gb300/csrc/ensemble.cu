@@ -30,6 +30,11 @@ static int fail(int rc, const char *fmt, ...) {
   return rc;
 }
 
+namespace swarm {
+// lets other translation units of the library report through swarm_last_error()
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace swarm
+
 #define CK(call)                                                                                        \
   do {                                                                                                  \
     cudaError_t e_ = (call);                                                                            \

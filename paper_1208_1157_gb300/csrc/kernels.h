@@ -25,6 +25,8 @@ cudaError_t launch_mvs_persistent(const BinView *d_bins, const int4 *d_work, int
                                   int grid, cudaStream_t st);
 int mvs_persistent_max_blocks_per_sm();
 
+void set_last_error(const char *msg);
+
 cudaError_t launch_fp64_peak(double *out, long long iters, int grid, int block, cudaStream_t st);
 
 }  // namespace swarm

@@ -27,6 +27,7 @@ EXPORTS = (
     "swarm_synchronize", "swarm_set_state", "swarm_query_state", "swarm_query_state_dev", "swarm_query_diagnostics",
     "swarm_query_log", "swarm_query_stats", "swarm_ensemble_size", "swarm_destroy_ensemble", "swarm_tuner_choice",
     "swarm_tuner_load", "swarm_tuner_save", "swarm_fp64_peak", "swarm_last_error", "swarm_version",
+    "swarm_hermite_integrate_noalloc",
 )
 
 
