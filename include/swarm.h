@@ -139,6 +139,51 @@ int swarm_query_stats(const swarm_ensemble *ens, swarm_stats *out);
 int32_t swarm_ensemble_size(const swarm_ensemble *ens);
 void swarm_destroy_ensemble(swarm_ensemble *ens);
 
+/* ------------------------------------------------------------------ serving */
+/* Continuous batching (the serving layer above the integrator; the paper's Algorithm 1
+ * loop generalized to requests that arrive while others run).  Requests of 1..4096
+ * systems with one body count n and one integrator are queued by swarm_server_submit;
+ * each swarm_server_step (1) admits queued requests, in arrival order, whose pool
+ * (integrator, n) has enough free slots — pools are allocated on demand within
+ * device_bytes (0 = no budget), empty pools are released when the budget is short —
+ * (2) advances every occupied slot by at most quantum_steps steps toward its own t_end in
+ * one persistent launch per integrator, and (3) retires requests whose systems all reached
+ * t_end or stopped, copying their results to host memory and freeing their slots for
+ * the next admissions.  A system takes the same steps as it would alone (steps of dt, the
+ * last one shortened to land on t_end), so results do not depend on the mix.  Not
+ * thread-safe: one thread drives a server. */
+typedef struct swarm_server swarm_server;
+typedef struct {
+  int32_t slots_per_pool;   /* systems per (integrator, n) pool */
+  int32_t quantum_steps;    /* steps per scheduling round */
+  double hermite_dt, mvs_dt;
+  double ce_hill_factor, eject_radius; /* as swarm_set_stop */
+  int64_t device_bytes;     /* budget for all pools, 0 = unlimited */
+} swarm_server_config;
+typedef struct {
+  int64_t submitted, admitted, completed, queued;
+  int64_t occupied_slots, pool_slots, device_bytes;
+  int64_t quanta, system_steps, pair_evaluations;
+  double kernel_ms;
+} swarm_server_stats;
+enum swarm_request_state { SWARM_REQ_QUEUED = 0, SWARM_REQ_RUNNING = 1, SWARM_REQ_DONE = 2 };
+
+int swarm_server_create(const swarm_server_config *cfg, void *cuda_stream, swarm_server **out);
+/* Host arrays in the creation layout ([n_sys*n_body][3]); copied, so the caller may reuse
+ * them on return.  *id receives the request id. */
+int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_body, const double *mass, const double *pos,
+                        const double *vel, double t0, double t_end, int integrator, int64_t *id);
+/* One scheduling round (admit, advance, retire); *n_completed = requests finished in it. */
+int swarm_server_step(swarm_server *sv, int32_t *n_completed);
+/* State of a request; when DONE, copies its final state into the host arrays (any may be
+ * NULL) and its latency (submit to retirement, seconds). */
+int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, double *pos, double *vel, double *time,
+                      int32_t *status, double *latency_s);
+/* Forget a finished request (frees its host copy of the results). */
+int swarm_server_release(swarm_server *sv, int64_t id);
+int swarm_server_query(const swarm_server *sv, swarm_server_stats *out);
+void swarm_server_destroy(swarm_server *sv);
+
 /* ------------------------------------------------------------------ tuner */
 /* Mapping the autotuner chose for (n, integrator, n_sys); measures on first use. */
 int swarm_tuner_choice(int32_t n, int integrator, int32_t n_sys, void *cuda_stream, int32_t *mapping,

@@ -21,6 +21,7 @@ struct BinView {
   double *x, *v, *m, *t;
   int32_t *status;
   int32_t *gidx;  // ensemble-wide index of bin system s (log buffer rows)
+  const double *t_end = nullptr;  // per-system end time (serving slots); null: the call's
 };
 
 struct StepParams {
@@ -35,6 +36,8 @@ struct StepParams {
   int32_t *log_count;    // [n_sys_total] records written so far (ring position)
   unsigned long long *counters;  // [0] system-steps, [1] pair evaluations, [2] Kepler iterations
   int *work_next;        // dynamic work-list head (persistent multi-bin launch)
+  int max_steps = 0;     // cap on the steps one launch takes per system (0: none)
+  const double *t_end_dev = nullptr;  // end time read from device memory (graph replays)
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -66,6 +69,39 @@ __device__ __forceinline__ StepPlan plan_steps(double t, double t_end, double dt
   p.N = p.exact ? (long long)Nr : (long long)ceil(D);
   p.h_last = p.exact ? dt : t_end - (t + (double)(p.N - 1) * dt);
   return p;
+}
+
+// What one launch does for one system: N steps toward its end time; `full` when the
+// launch reaches that end time (then the last step may be shortened, R9), otherwise N is
+// the launch's step cap and every step has length dt.
+struct LaunchPlan {
+  int N;
+  int full;
+  int exact;
+  double h_last;
+  double t_end;
+};
+__device__ __forceinline__ LaunchPlan launch_plan(const BinView &B, const StepParams &P, int s, double t0,
+                                                  bool runnable) {
+  const double te = B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
+  const StepPlan p = plan_steps(t0, te, P.dt);
+  LaunchPlan L;
+  L.t_end = te;
+  L.full = 1;
+  L.exact = p.exact;
+  L.h_last = p.h_last;
+  L.N = runnable ? (int)p.N : 0;
+  if (P.max_steps > 0 && L.N > P.max_steps) {
+    L.N = P.max_steps;
+    L.full = 0;
+    L.exact = 1;
+    L.h_last = P.dt;
+  }
+  return L;
+}
+// time after step k of a launch
+__device__ __forceinline__ double step_time(const LaunchPlan &L, int k, double t0, double dt) {
+  return (k == L.N && L.full) ? L.t_end : t0 + (double)k * dt;
 }
 
 }  // namespace swarm

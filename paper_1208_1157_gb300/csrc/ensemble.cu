@@ -89,6 +89,11 @@ struct swarm_ensemble {
   double ce = 0.0, eject = 0.0;
   double t_lo = 0.0, t_hi = 0.0;  // range of runnable systems' times (step-count guard)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // chunked launches (SWARM_OPT_STEPS_PER_LAUNCH): captured once, replayed
+  cudaStream_t cap_stream = nullptr;
+  double *d_tend = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
   swarm_stats stats{};
   bool stats_pending = false;
   int last_integrator = 0;
@@ -191,6 +196,9 @@ static void free_all(swarm_ensemble *e) {
   if (e->plain_block) cudaFree(e->plain_block);
   if (e->ev0) cudaEventDestroy(e->ev0);
   if (e->ev1) cudaEventDestroy(e->ev1);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  if (e->d_tend) cudaFree(e->d_tend);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
 }
 
 static int upload_state(swarm_ensemble *e, const double *pos, const double *vel, const double *mass,
@@ -297,6 +305,8 @@ extern "C" int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const
   CKC(cudaMalloc(&e->d_work_next, sizeof(int) * 4));
   CKC(cudaEventCreate(&e->ev0));
   CKC(cudaEventCreate(&e->ev1));
+  CKC(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+  CKC(cudaMalloc(&e->d_tend, sizeof(double)));
   std::vector<double> tt(n_sys, t0);
   std::vector<int32_t> ss(n_sys, SWARM_SYS_ACTIVE);
   if ((rc = upload_state(e, pos, vel, mass, tt.data(), ss.data()))) return cleanup(rc);
@@ -448,6 +458,32 @@ static int ensure_plain(swarm_ensemble *e, int S_pad, int n) {
   return SWARM_OK;
 }
 
+// Replays `record` (which enqueues kernels on the stream it is given) from a CUDA graph
+// captured on the ensemble's capture stream; re-captures when `key` changes.
+template <class F>
+static int replay_graph(swarm_ensemble *e, const std::vector<double> &key, F record) {
+  if (!e->graph || key != e->graph_key) {
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
+    e->graph_key.clear();
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = record(e->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CK(ce);
+    cudaError_t ie = cudaGraphInstantiate(&e->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+    e->graph_key = key;
+  }
+  CK(cudaGraphLaunch(e->graph, e->stream));
+  return SWARM_OK;
+}
+
 // Plain baseline: per bin, one prepare launch and one launch per step.
 static int run_plain(swarm_ensemble *e, const StepParams &P) {
   cudaStream_t st = e->stream;
@@ -462,9 +498,23 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
     int nmax = 0;
     CK(cudaMemcpyAsync(&nmax, W.max_steps, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (int k = 1; k <= nmax; k++) {
-      CK(launch_plain(b.view(), P, W, k, st));
-      e->launches++;
+    if (e->steps_per_launch > 0 && nmax > 0) {
+      // the per-step launches, captured once per (bin, step count) and replayed
+      std::vector<double> key = {1.0, (double)b.n, (double)b.S, (double)nmax, P.dt, (double)P.n_corr, P.ce_factor,
+                                 P.eject2, (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)b.x,
+                                 (double)(uintptr_t)W.a0};
+      BinView bv = b.view();
+      int rc2 = replay_graph(e, key, [&](cudaStream_t cs) -> int {
+        for (int k = 1; k <= nmax; k++) CK(launch_plain(bv, P, W, k, cs));
+        return SWARM_OK;
+      });
+      if (rc2) return rc2;
+      e->launches += nmax;
+    } else {
+      for (int k = 1; k <= nmax; k++) {
+        CK(launch_plain(b.view(), P, W, k, st));
+        e->launches++;
+      }
     }
   }
   return SWARM_OK;
@@ -495,10 +545,37 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   int need = (e->nwork + 3) / 4;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), e->stream));
-  if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
-  else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
-  e->launches++;
+  if (e->steps_per_launch <= 0) {
+    CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), e->stream));
+    if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
+    else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
+    e->launches++;
+    return SWARM_OK;
+  }
+  // Chunked: K launches of at most L steps each, all with identical parameters (the end
+  // time is read from device memory), captured into one CUDA graph and replayed.
+  const int L = e->steps_per_launch;
+  const double span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
+  const long long nmax = (long long)std::ceil(span - 1e-9);
+  const int K = (int)std::max(1LL, (nmax + L - 1) / L);
+  StepParams Q = P;
+  Q.max_steps = L;
+  Q.t_end_dev = e->d_tend;
+  const double te = P.t_end;
+  CK(cudaMemcpyAsync(e->d_tend, &te, sizeof(double), cudaMemcpyHostToDevice, e->stream));
+  std::vector<double> key = {2.0, (double)K, (double)L, (double)integrator, (double)grid, (double)e->nwork, P.dt,
+                             (double)P.n_corr, P.ce_factor, P.eject2, (double)P.log_interval, (double)P.log_cap};
+  for (int m : maps) key.push_back((double)m);
+  rc = replay_graph(e, key, [&](cudaStream_t cs) -> int {
+    for (int k = 0; k < K; k++) {
+      CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
+      if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+      else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+    }
+    return SWARM_OK;
+  });
+  if (rc) return rc;
+  e->launches += K;
   return SWARM_OK;
 }
 

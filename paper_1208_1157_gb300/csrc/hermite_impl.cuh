@@ -39,8 +39,8 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
   const int st0 = B.status[s];
   const double m0 = shfl(m, base);
   const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
-  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
-  const int Ns = runnable ? (int)plan.N : 0;
+  const LaunchPlan plan = launch_plan(B, P, s, t0, runnable);
+  const int Ns = plan.N;
   const int Nmax = __reduce_max_sync(FULL, Ns);
   if (Nmax == 0) {
     if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
@@ -117,7 +117,7 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
     const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
     const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
     const int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-    const double tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    const double tk = step_time(plan, k, t0, P.dt);
     if (active && code) {
       if (sys_ok) {
 #pragma unroll
@@ -147,8 +147,8 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
       }
     }
     if (b == 0) {
-      if (Ns > 0) B.t[s] = P.t_end;
-      B.status[s] = SWARM_SYS_DONE;
+      if (Ns > 0) B.t[s] = step_time(plan, Ns, t0, P.dt);
+      B.status[s] = plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
     }
   }
   if (P.counters && sys_ok && b == 0 && steps_done > 0) {
@@ -176,8 +176,8 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
   }
   const double t0 = B.t[s];
   if (B.status[s] > SWARM_SYS_DONE) return;
-  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
-  const int Ns = (int)plan.N;
+  const LaunchPlan plan = launch_plan(B, P, s, t0, true);
+  const int Ns = plan.N;
   if (Ns == 0) {
     B.status[s] = SWARM_SYS_DONE;
     return;
@@ -227,7 +227,7 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
         v[i][c] = vk[i][c];
       }
     steps_done = k;
-    tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    tk = step_time(plan, k, t0, P.dt);
     bool nf = false, ej = false, ce = false;
 #pragma unroll
     for (int i = 0; i < N; i++)
@@ -256,7 +256,7 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
       B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
     }
   B.t[s] = tk;
-  B.status[s] = code ? code : SWARM_SYS_DONE;
+  B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
   if (P.counters) {
     constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
     atomicAdd(&P.counters[0], (unsigned long long)steps_done);

@@ -381,8 +381,8 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
   const int st0 = B.status[s];
   const double m0 = shfl(m, base);
   const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
-  const StepPlan plan = plan_steps(t0, P.t_end, P.dt);
-  const int Ns = runnable ? (int)plan.N : 0;
+  const LaunchPlan plan = launch_plan(B, P, s, t0, runnable);
+  const int Ns = plan.N;
   const int Nmax = __reduce_max_sync(FULL, Ns);
   if (Nmax == 0) {
     if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
@@ -500,7 +500,7 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
     const int code = bkn ? SWARM_SYS_KEPLER_NOCONV
                          : bnf ? SWARM_SYS_NONFINITE
                                : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-    const double tk = (k == Ns) ? P.t_end : t0 + (double)k * P.dt;
+    const double tk = step_time(plan, k, t0, P.dt);
     const bool want_log = P.log_interval > 0 && (k % P.log_interval) == 0;
     if (__any_sync(FULL, active && code != 0) || want_log) {
       double xo[3], vo[3];
@@ -541,8 +541,8 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
         }
       }
       if (b == 0) {
-        if (Ns > 0) B.t[s] = P.t_end;
-        B.status[s] = SWARM_SYS_DONE;
+        if (Ns > 0) B.t[s] = step_time(plan, Ns, t0, P.dt);
+        B.status[s] = plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
       }
     }
   }

@@ -1,0 +1,484 @@
+// Continuous-batching server: integration requests of different sizes, body counts and
+// integrators share the GPU.  Their systems occupy slots of device-resident pools (one
+// pool per integrator and body count); every scheduling round admits queued requests
+// into free slots (within a device-memory budget), advances all occupied slots by one
+// quantum of at most Q steps in one persistent launch per integrator, then retires the
+// requests whose systems all reached their end time or stopped and frees their slots for
+// the next admissions.  A request's systems take exactly the steps they would take alone
+// (full steps of dt, the last one shortened to land on its t_end), so its result does not
+// depend on what else is in flight.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tuner.h"
+
+using namespace swarm;
+
+namespace {
+
+constexpr int kFree = 7;  // slot status of an unoccupied slot (never runnable)
+using Clock = std::chrono::steady_clock;
+
+int sfail(int rc, const std::string &m) {
+  set_last_error(m.c_str());
+  return rc;
+}
+#define SCK(call)                                                                             \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return sfail(SWARM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Pool {
+  int integ = 0, n = 0, cap = 0;
+  void *block = nullptr;
+  BinView view{};
+  double *t_end = nullptr;
+  std::vector<int> free_slots;
+  std::vector<int64_t> owner;  // request id per slot, -1 if free
+  size_t bytes = 0;
+};
+
+struct Request {
+  int64_t id = 0;
+  int n_sys = 0, n = 0, integ = 0;
+  double t0 = 0, t_end = 0;
+  std::vector<double> mass, pos, vel;  // caller layout
+  int state = SWARM_REQ_QUEUED;
+  Pool *pool = nullptr;
+  std::vector<int> slots;
+  Clock::time_point submitted, finished;
+  std::vector<double> out_pos, out_vel, out_time;
+  std::vector<int32_t> out_status;
+};
+
+// scatter one request's systems into pool slots
+__global__ void admit_kernel(BinView B, double *t_end_slots, const int *__restrict__ slots, int n_sys,
+                             const double *__restrict__ pos, const double *__restrict__ vel,
+                             const double *__restrict__ mass, double t0, double t_end) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_sys) return;
+  const int s = slots[i], n = B.n;
+  for (int b = 0; b < n; b++) {
+    for (int c = 0; c < 3; c++) {
+      B.x[(size_t)(c * n + b) * B.S_pad + s] = pos[3 * ((size_t)i * n + b) + c];
+      B.v[(size_t)(c * n + b) * B.S_pad + s] = vel[3 * ((size_t)i * n + b) + c];
+    }
+    B.m[(size_t)b * B.S_pad + s] = mass[(size_t)i * n + b];
+  }
+  B.t[s] = t0;
+  B.status[s] = SWARM_SYS_ACTIVE;
+  t_end_slots[s] = t_end;
+}
+
+// gather one finished request and free its slots
+__global__ void retire_kernel(BinView B, const int *__restrict__ slots, int n_sys, double *__restrict__ pos,
+                              double *__restrict__ vel, double *__restrict__ time, int32_t *__restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_sys) return;
+  const int s = slots[i], n = B.n;
+  for (int b = 0; b < n; b++)
+    for (int c = 0; c < 3; c++) {
+      pos[3 * ((size_t)i * n + b) + c] = B.x[(size_t)(c * n + b) * B.S_pad + s];
+      vel[3 * ((size_t)i * n + b) + c] = B.v[(size_t)(c * n + b) * B.S_pad + s];
+    }
+  time[i] = B.t[s];
+  status[i] = B.status[s];
+  B.status[s] = kFree;
+}
+
+__global__ void fill_status_kernel(int32_t *st, int n, int v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) st[i] = v;
+}
+
+}  // namespace
+
+struct swarm_server {
+  swarm_server_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::map<std::pair<int, int>, std::unique_ptr<Pool>> pools;
+  std::map<int64_t, std::unique_ptr<Request>> reqs;
+  std::deque<int64_t> queue;
+  int64_t next_id = 1;
+  size_t bytes_used = 0;
+  // staging for one request (caller layout) and its slot list
+  double *d_stage = nullptr;
+  int *d_slots = nullptr;
+  size_t stage_doubles = 0;
+  std::vector<int32_t> h_status;
+  // per-integrator launch resources
+  struct Launch {
+    BinView *d_bins = nullptr;
+    int4 *d_work = nullptr;
+    int nwork = 0, nbins = 0, cap_work = 0, cap_bins = 0;
+    int *d_next = nullptr;
+    bool dirty = true;
+  } launch[4];
+  unsigned long long *d_counters = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  swarm_server_stats stats{};
+};
+
+static size_t pool_bytes(int n, int cap) {
+  return sizeof(double) * (size_t)cap * (7 * n + 2) + 2 * sizeof(int32_t) * (size_t)cap;
+}
+
+static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
+  auto key = std::make_pair(integ, n);
+  auto it = sv->pools.find(key);
+  if (it != sv->pools.end()) {
+    *out = it->second.get();
+    return SWARM_OK;
+  }
+  *out = nullptr;
+  const int cap = (sv->cfg.slots_per_pool + 31) / 32 * 32;
+  const size_t bytes = pool_bytes(n, cap);
+  if (sv->cfg.device_bytes > 0 && sv->bytes_used + bytes > (size_t)sv->cfg.device_bytes) {
+    // over the memory budget: release pools that hold no system, then try again later
+    SCK(cudaStreamSynchronize(sv->stream));
+    for (auto jt = sv->pools.begin(); jt != sv->pools.end();) {
+      Pool *q = jt->second.get();
+      if ((int)q->free_slots.size() == q->cap && sv->bytes_used + bytes > (size_t)sv->cfg.device_bytes) {
+        cudaFree(q->block);
+        sv->bytes_used -= q->bytes;
+        sv->launch[q->integ].dirty = true;
+        jt = sv->pools.erase(jt);
+      } else {
+        ++jt;
+      }
+    }
+    if (sv->bytes_used + bytes > (size_t)sv->cfg.device_bytes) return SWARM_OK;  // wait for slots to free
+  }
+  auto p = std::make_unique<Pool>();
+  p->integ = integ;
+  p->n = n;
+  p->cap = cap;
+  p->bytes = bytes;
+  SCK(cudaMalloc(&p->block, bytes));
+  double *d = (double *)p->block;
+  p->view.n = n;
+  p->view.S = cap;
+  p->view.S_pad = cap;
+  p->view.x = d;
+  p->view.v = d + (size_t)3 * n * cap;
+  p->view.m = d + (size_t)6 * n * cap;
+  p->view.t = d + (size_t)7 * n * cap;
+  p->t_end = d + (size_t)(7 * n + 1) * cap;
+  p->view.t_end = p->t_end;
+  p->view.status = (int32_t *)(d + (size_t)(7 * n + 2) * cap);
+  p->view.gidx = p->view.status + cap;
+  SCK(cudaMemsetAsync(p->block, 0, bytes, sv->stream));
+  fill_status_kernel<<<(cap + 255) / 256, 256, 0, sv->stream>>>(p->view.status, cap, kFree);
+  SCK(cudaGetLastError());
+  p->free_slots.resize(cap);
+  for (int i = 0; i < cap; i++) p->free_slots[i] = cap - 1 - i;  // pop_back gives 0, 1, 2, ...
+  p->owner.assign(cap, -1);
+  sv->bytes_used += bytes;
+  sv->launch[integ].dirty = true;
+  *out = p.get();
+  sv->pools[key] = std::move(p);
+  return SWARM_OK;
+}
+
+static int rebuild_launch(swarm_server *sv, int integ) {
+  auto &L = sv->launch[integ];
+  if (!L.dirty) return SWARM_OK;
+  std::vector<BinView> views;
+  std::vector<int4> work;
+  for (auto &kv : sv->pools) {
+    Pool *p = kv.second.get();
+    if (p->integ != integ) continue;
+    int32_t mapping = SWARM_MAP_BODY_PER_LANE, ctas = 0;
+    int rc = tuner_choice_internal(p->n, integ, p->cap, sv->stream, &mapping, &ctas);
+    if (rc) return rc;
+    if (integ != SWARM_HERMITE4 || p->n > 4) mapping = SWARM_MAP_BODY_PER_LANE;
+    const int per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : 32 / p->n;
+    const int units = (p->cap + per - 1) / per;
+    for (int u = 0; u < units; u++) work.push_back(make_int4((int)views.size(), u, mapping, p->n));
+    views.push_back(p->view);
+  }
+  std::stable_sort(work.begin(), work.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
+  if ((int)views.size() > L.cap_bins) {
+    if (L.d_bins) cudaFree(L.d_bins);
+    L.d_bins = nullptr;
+    SCK(cudaMalloc(&L.d_bins, sizeof(BinView) * std::max<size_t>(views.size(), 16)));
+    L.cap_bins = (int)std::max<size_t>(views.size(), 16);
+  }
+  if ((int)work.size() > L.cap_work) {
+    if (L.d_work) cudaFree(L.d_work);
+    L.d_work = nullptr;
+    SCK(cudaMalloc(&L.d_work, sizeof(int4) * work.size()));
+    L.cap_work = (int)work.size();
+  }
+  if (!L.d_next) SCK(cudaMalloc(&L.d_next, sizeof(int)));
+  if (!views.empty()) SCK(cudaMemcpyAsync(L.d_bins, views.data(), sizeof(BinView) * views.size(), cudaMemcpyHostToDevice, sv->stream));
+  if (!work.empty()) SCK(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, sv->stream));
+  SCK(cudaStreamSynchronize(sv->stream));  // host vectors go out of scope
+  L.nwork = (int)work.size();
+  L.nbins = (int)views.size();
+  L.dirty = false;
+  return SWARM_OK;
+}
+
+extern "C" int swarm_server_create(const swarm_server_config *cfg, void *cuda_stream, swarm_server **out) {
+  if (!cfg || !out) return sfail(SWARM_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (cfg->slots_per_pool < 1 || cfg->slots_per_pool > (1 << 24) || cfg->quantum_steps < 1 ||
+      !(cfg->hermite_dt > 0) || !(cfg->mvs_dt > 0) || !std::isfinite(cfg->ce_hill_factor) ||
+      !std::isfinite(cfg->eject_radius) || cfg->device_bytes < 0)
+    return sfail(SWARM_EINVAL, "bad server configuration");
+  auto sv = std::make_unique<swarm_server>();
+  sv->cfg = *cfg;
+  sv->stream = (cudaStream_t)cuda_stream;
+  sv->stage_doubles = (size_t)4096 * SWARM_MAX_N * 7 + 4096 * 2;
+  SCK(cudaMalloc(&sv->d_stage, sizeof(double) * sv->stage_doubles));
+  SCK(cudaMalloc(&sv->d_slots, sizeof(int) * 4096));
+  SCK(cudaMalloc(&sv->d_counters, sizeof(unsigned long long) * 4));
+  SCK(cudaEventCreate(&sv->ev0));
+  SCK(cudaEventCreate(&sv->ev1));
+  *out = sv.release();
+  return SWARM_OK;
+}
+
+extern "C" void swarm_server_destroy(swarm_server *sv) {
+  if (!sv) return;
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  else cudaDeviceSynchronize();
+  for (auto &kv : sv->pools) cudaFree(kv.second->block);
+  for (auto &L : sv->launch) {
+    if (L.d_bins) cudaFree(L.d_bins);
+    if (L.d_work) cudaFree(L.d_work);
+    if (L.d_next) cudaFree(L.d_next);
+  }
+  cudaFree(sv->d_stage);
+  cudaFree(sv->d_slots);
+  cudaFree(sv->d_counters);
+  cudaEventDestroy(sv->ev0);
+  cudaEventDestroy(sv->ev1);
+  delete sv;
+}
+
+extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_body, const double *mass,
+                                   const double *pos, const double *vel, double t0, double t_end, int integrator,
+                                   int64_t *id) {
+  if (!sv || !mass || !pos || !vel || !id) return sfail(SWARM_EINVAL, "NULL argument");
+  if (n_sys < 1 || n_sys > 4096) return sfail(SWARM_EINVAL, "a request holds 1..4096 systems");
+  if (n_body < SWARM_MIN_N || n_body > SWARM_MAX_N) return sfail(SWARM_EINVAL, "n_body must be in 2..15");
+  if (integrator < SWARM_HERMITE4 || integrator > SWARM_MVS_JACOBI) return sfail(SWARM_EINVAL, "unknown integrator");
+  if (!std::isfinite(t0) || !std::isfinite(t_end)) return sfail(SWARM_EINVAL, "t0 and t_end must be finite");
+  if (n_sys > ((sv->cfg.slots_per_pool + 31) / 32 * 32)) return sfail(SWARM_EINVAL, "request larger than a slot pool");
+  const size_t nb = (size_t)n_sys * n_body;
+  for (size_t i = 0; i < nb; i++)
+    if (!(mass[i] > 0) || !std::isfinite(mass[i])) return sfail(SWARM_EINVAL, "masses must be positive and finite");
+  for (size_t i = 0; i < 3 * nb; i++)
+    if (!std::isfinite(pos[i]) || !std::isfinite(vel[i])) return sfail(SWARM_EINVAL, "non-finite position or velocity");
+  auto r = std::make_unique<Request>();
+  r->id = sv->next_id++;
+  r->n_sys = n_sys;
+  r->n = n_body;
+  r->integ = integrator;
+  r->t0 = t0;
+  r->t_end = t_end;
+  r->mass.assign(mass, mass + nb);
+  r->pos.assign(pos, pos + 3 * nb);
+  r->vel.assign(vel, vel + 3 * nb);
+  r->submitted = Clock::now();
+  *id = r->id;
+  sv->queue.push_back(r->id);
+  sv->reqs[r->id] = std::move(r);
+  sv->stats.submitted++;
+  return SWARM_OK;
+}
+
+static int admit(swarm_server *sv) {
+  for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+    Request *r = sv->reqs[*it].get();
+    Pool *p = nullptr;
+    int rc = make_pool(sv, r->integ, r->n, &p);
+    if (rc) return rc;
+    if (!p || (int)p->free_slots.size() < r->n_sys) {  // not enough memory/slots yet: later
+      ++it;
+      continue;
+    }
+    r->slots.resize(r->n_sys);
+    for (int i = 0; i < r->n_sys; i++) {
+      r->slots[i] = p->free_slots.back();
+      p->free_slots.pop_back();
+      p->owner[r->slots[i]] = r->id;
+    }
+    r->pool = p;
+    const size_t nb = (size_t)r->n_sys * r->n;
+    double *dpos = sv->d_stage, *dvel = dpos + 3 * nb, *dmass = dvel + 3 * nb;
+    SCK(cudaMemcpyAsync(dpos, r->pos.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaMemcpyAsync(dvel, r->vel.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaMemcpyAsync(dmass, r->mass.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaMemcpyAsync(sv->d_slots, r->slots.data(), sizeof(int) * r->n_sys, cudaMemcpyHostToDevice, sv->stream));
+    admit_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(p->view, p->t_end, sv->d_slots, r->n_sys, dpos, dvel,
+                                                                  dmass, r->t0, r->t_end);
+    SCK(cudaGetLastError());
+    SCK(cudaStreamSynchronize(sv->stream));  // staging is reused by the next admission
+    r->state = SWARM_REQ_RUNNING;
+    r->pos.clear();
+    r->vel.clear();
+    sv->stats.admitted++;
+    it = sv->queue.erase(it);
+  }
+  return SWARM_OK;
+}
+
+static int retire(swarm_server *sv, int32_t *n_completed) {
+  // which requests are complete: every slot DONE or stopped
+  std::map<int64_t, int> pending;  // request id -> slots not finished
+  for (auto &kv : sv->pools) {
+    Pool *p = kv.second.get();
+    bool any = false;
+    for (int64_t o : p->owner)
+      if (o >= 0) {
+        any = true;
+        break;
+      }
+    if (!any) continue;
+    sv->h_status.resize(p->cap);
+    SCK(cudaMemcpyAsync(sv->h_status.data(), p->view.status, sizeof(int32_t) * p->cap, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaStreamSynchronize(sv->stream));
+    for (int s = 0; s < p->cap; s++) {
+      int64_t o = p->owner[s];
+      if (o < 0) continue;
+      int &c = pending[o];
+      if (sv->h_status[s] == SWARM_SYS_ACTIVE) c++;
+    }
+  }
+  for (auto &kv : pending) {
+    if (kv.second) continue;
+    Request *r = sv->reqs[kv.first].get();
+    Pool *p = r->pool;
+    const size_t nb = (size_t)r->n_sys * r->n;
+    double *dpos = sv->d_stage, *dvel = dpos + 3 * nb, *dtime = dvel + 3 * nb;
+    int32_t *dstat = (int32_t *)(dtime + r->n_sys);
+    SCK(cudaMemcpyAsync(sv->d_slots, r->slots.data(), sizeof(int) * r->n_sys, cudaMemcpyHostToDevice, sv->stream));
+    retire_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(p->view, sv->d_slots, r->n_sys, dpos, dvel, dtime, dstat);
+    SCK(cudaGetLastError());
+    r->out_pos.resize(3 * nb);
+    r->out_vel.resize(3 * nb);
+    r->out_time.resize(r->n_sys);
+    r->out_status.resize(r->n_sys);
+    SCK(cudaMemcpyAsync(r->out_pos.data(), dpos, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaMemcpyAsync(r->out_vel.data(), dvel, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaMemcpyAsync(r->out_time.data(), dtime, sizeof(double) * r->n_sys, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaMemcpyAsync(r->out_status.data(), dstat, sizeof(int32_t) * r->n_sys, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaStreamSynchronize(sv->stream));
+    for (int s : r->slots) {
+      p->owner[s] = -1;
+      p->free_slots.push_back(s);
+    }
+    r->slots.clear();
+    r->state = SWARM_REQ_DONE;
+    r->finished = Clock::now();
+    sv->stats.completed++;
+    (*n_completed)++;
+  }
+  return SWARM_OK;
+}
+
+extern "C" int swarm_server_step(swarm_server *sv, int32_t *n_completed) {
+  if (!sv || !n_completed) return sfail(SWARM_EINVAL, "NULL argument");
+  *n_completed = 0;
+  int rc = admit(sv);
+  if (rc) return rc;
+  bool ran = false;
+  SCK(cudaMemsetAsync(sv->d_counters, 0, sizeof(unsigned long long) * 4, sv->stream));
+  SCK(cudaEventRecord(sv->ev0, sv->stream));
+  for (int integ = SWARM_HERMITE4; integ <= SWARM_MVS_JACOBI; integ++) {
+    bool occupied = false;
+    for (auto &kv : sv->pools)
+      if (kv.second->integ == integ && (int)kv.second->free_slots.size() < kv.second->cap) occupied = true;
+    if (!occupied) continue;
+    if ((rc = rebuild_launch(sv, integ))) return rc;
+    auto &L = sv->launch[integ];
+    StepParams P{};
+    P.t_end = 0;
+    P.dt = integ == SWARM_HERMITE4 ? sv->cfg.hermite_dt : sv->cfg.mvs_dt;
+    P.n_corr = 2;
+    P.integrator = integ;
+    P.ce_factor = sv->cfg.ce_hill_factor;
+    P.eject2 = sv->cfg.eject_radius > 0 ? sv->cfg.eject_radius * sv->cfg.eject_radius : 0.0;
+    P.counters = sv->d_counters;
+    P.work_next = L.d_next;
+    P.max_steps = sv->cfg.quantum_steps;
+    int maxb = integ == SWARM_HERMITE4 ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = std::max(1, std::min(sms * std::max(maxb, 1), (L.nwork + 3) / 4));
+    SCK(cudaMemsetAsync(L.d_next, 0, sizeof(int), sv->stream));
+    if (integ == SWARM_HERMITE4) SCK(launch_hermite_persistent(L.d_bins, L.d_work, L.nwork, P, grid, sv->stream));
+    else SCK(launch_mvs_persistent(L.d_bins, L.d_work, L.nwork, P, grid, sv->stream));
+    ran = true;
+  }
+  SCK(cudaEventRecord(sv->ev1, sv->stream));
+  SCK(cudaStreamSynchronize(sv->stream));
+  if (ran) {
+    unsigned long long c[4];
+    SCK(cudaMemcpy(c, sv->d_counters, sizeof c, cudaMemcpyDeviceToHost));
+    float ms = 0;
+    SCK(cudaEventElapsedTime(&ms, sv->ev0, sv->ev1));
+    sv->stats.system_steps += (int64_t)c[0];
+    sv->stats.pair_evaluations += (int64_t)c[1];
+    sv->stats.kernel_ms += ms;
+    sv->stats.quanta++;
+  }
+  return retire(sv, n_completed);
+}
+
+extern "C" int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, double *pos, double *vel,
+                                 double *time, int32_t *status, double *latency_s) {
+  if (!sv || !state) return sfail(SWARM_EINVAL, "NULL argument");
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(SWARM_EINVAL, "unknown or released request id");
+  Request *r = it->second.get();
+  *state = r->state;
+  if (r->state != SWARM_REQ_DONE) return SWARM_OK;
+  const size_t nb = (size_t)r->n_sys * r->n;
+  if (pos) memcpy(pos, r->out_pos.data(), sizeof(double) * 3 * nb);
+  if (vel) memcpy(vel, r->out_vel.data(), sizeof(double) * 3 * nb);
+  if (time) memcpy(time, r->out_time.data(), sizeof(double) * r->n_sys);
+  if (status) memcpy(status, r->out_status.data(), sizeof(int32_t) * r->n_sys);
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->finished - r->submitted).count();
+  return SWARM_OK;
+}
+
+extern "C" int swarm_server_release(swarm_server *sv, int64_t id) {
+  if (!sv) return sfail(SWARM_EINVAL, "NULL server");
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(SWARM_EINVAL, "unknown request id");
+  if (it->second->state != SWARM_REQ_DONE) return sfail(SWARM_ESTATE, "request is not finished");
+  sv->reqs.erase(it);
+  return SWARM_OK;
+}
+
+extern "C" int swarm_server_query(const swarm_server *sv, swarm_server_stats *out) {
+  if (!sv || !out) return sfail(SWARM_EINVAL, "NULL argument");
+  *out = sv->stats;
+  out->queued = (int64_t)sv->queue.size();
+  int64_t occ = 0, cap = 0;
+  for (auto &kv : sv->pools) {
+    occ += kv.second->cap - (int64_t)kv.second->free_slots.size();
+    cap += kv.second->cap;
+  }
+  out->occupied_slots = occ;
+  out->pool_slots = cap;
+  out->device_bytes = (int64_t)sv->bytes_used;
+  return SWARM_OK;
+}

@@ -150,3 +150,26 @@ def test_ragged_full_size_sampled():
     rows = np.concatenate([np.arange(offs[s], offs[s + 1]) for s in idx])
     gs = {"pos": g["pos"][rows], "vel": g["vel"][rows], "time": g["time"][idx], "status": g["status"][idx]}
     assert_parity(sub, gs, o)
+
+
+@pytest.mark.parametrize("mapping", [0, 3])
+def test_chunked_launches_replayed_from_a_cuda_graph(mapping):
+    # steps per launch = 64: the call becomes a captured graph of launches of <= 64 steps
+    # (persistent), or of single steps (plain); the second call replays the same graph
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.three_body(300, seed=15)
+    ref = run_gpu(ens, 1000 * DT, 1, DT, mapping=mapping)
+    with S.Ensemble(ens) as e:
+        e.set_option(S.OPT_MAPPING, mapping)
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, 64)
+        e.integrate(500 * DT, S.HERMITE4, DT)
+        first = e.stats()["kernel_launches"]
+        e.integrate(1000 * DT, S.HERMITE4, DT)
+        second = e.stats()["kernel_launches"]
+        got = e.state()
+    assert first == second == (8 if mapping == 0 else 501)  # plain: prepare + 500 steps
+    ex, ev = per_system_errors(ens, got, ref)
+    assert ex.max() <= 1e-14 and ev.max() <= 1e-14
+    np.testing.assert_allclose(got["time"], ref["time"], rtol=1e-14)
+    assert np.all(got["status"] == O.DONE)

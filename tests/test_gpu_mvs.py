@@ -70,3 +70,21 @@ def test_mvs_full_size_sampled():
     gs = {"pos": g["pos"].reshape(-1, 8, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 8, 3)[idx].reshape(-1, 3),
           "time": g["time"][idx], "status": g["status"][idx]}
     assert_parity(sub, gs, o, sens=sens)
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_mvs_chunked_launches(kind):
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.mvs_compact(64, seed=14)
+    ref = run_gpu(ens, 300 * DT, kind, DT, ce=3.0, ej=100.0)
+    with S.Ensemble(ens) as e:
+        e.set_stop(3.0, 100.0)
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, 50)
+        e.integrate(300 * DT, kind, DT)
+        assert e.stats()["kernel_launches"] == 6
+        got = e.state()
+    from gpu_util import per_system_errors
+    assert np.array_equal(got["status"], ref["status"])
+    ex, ev = per_system_errors(ens, got, ref)
+    assert ex.max() <= 1e-10 and ev.max() <= 1e-10

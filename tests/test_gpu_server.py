@@ -1,0 +1,113 @@
+"""Continuous batching: requests served in a mix give the same results as alone."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import per_system_errors
+from paper_1208_1157_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+HDT = 2 * math.pi * 1e-3
+MDT = 2 * math.pi / 20
+INTEG = {1: 1, 2: 2, 3: 3}
+
+
+def small_trace(seed=31, k=14):
+    rng = np.random.default_rng(seed)
+    trace = []
+    for r in range(k):
+        integ = int(rng.integers(1, 4))
+        n = int(rng.choice([3, 5, 8, 13]))
+        steps = int(rng.integers(20, 260)) if integ == 1 else int(rng.integers(10, 90))
+        dt = HDT if integ == 1 else MDT
+        trace.append({"id": r, "arrival_s": 0.004 * r, "n_sys": int(rng.integers(1, 150)), "n": n,
+                      "integrator": integ, "t_end": (steps + 0.37) * dt, "seed": 1000 + r})
+    return trace
+
+
+def alone(ens, t_end, integ, ce=3.0, ej=100.0):
+    from paper_1208_1157_gb300 import swarm as S
+
+    with S.Ensemble(ens) as e:
+        e.set_stop(ce, ej)
+        e.integrate(t_end, integ, HDT if integ == 1 else MDT)
+        return e.state()
+
+
+def check_same(trace, ens_list, out, tol=1e-10):
+    for r, q in enumerate(trace):
+        res = out["done"][r]
+        ref = alone(ens_list[r], q["t_end"], q["integrator"])
+        assert np.array_equal(res["status"], ref["status"]), f"request {r}"
+        np.testing.assert_allclose(res["time"], ref["time"], rtol=1e-13, atol=0)
+        ex, ev = per_system_errors(ens_list[r], res, ref)
+        assert ex.max() <= tol and ev.max() <= tol, (r, ex.max(), ev.max())
+
+
+def test_results_in_the_mix_equal_results_alone():
+    from paper_1208_1157_gb300 import server as SV
+
+    trace = small_trace()
+    ens_list = [ics.request_ensemble(q) for q in trace]
+    with SV.Server(slots_per_pool=512, quantum_steps=37) as sv:
+        out = SV.replay(sv, trace, ens_list, collect=True)
+        st = sv.stats()
+    assert st["completed"] == len(trace) and st["queued"] == 0
+    assert st["quanta"] > 1
+    check_same(trace, ens_list, out)
+
+
+def test_backfill_when_pools_are_full():
+    # pools of 64 slots: the 5-body Hermite requests below need 150 slots in total, so the
+    # later ones wait in the queue until earlier ones retire and free their slots
+    from paper_1208_1157_gb300 import server as SV
+
+    trace = [{"id": r, "arrival_s": 0.0, "n_sys": 50, "n": 5, "integrator": 1, "t_end": (40 + 30 * r) * HDT,
+              "seed": 2000 + r} for r in range(3)]
+    ens_list = [ics.request_ensemble(q) for q in trace]
+    with SV.Server(slots_per_pool=64, quantum_steps=25) as sv:
+        for q, e in zip(trace, ens_list):
+            sv.submit(e, q["t_end"], 1)
+        sv.step()
+        st = sv.stats()
+        assert st["admitted"] == 1 and st["queued"] == 2  # only one request fits at first
+        out = {"done": {}}
+        for _ in range(200):
+            sv.step()
+            if sv.stats()["completed"] == 3:
+                break
+        for r, q in enumerate(trace):
+            state, res = sv.poll(r + 1, q["n_sys"], q["n"])
+            assert state == SV.REQ_DONE
+            out["done"][r] = res
+    check_same(trace, ens_list, out)
+
+
+def test_memory_budget_releases_idle_pools():
+    from paper_1208_1157_gb300 import server as SV
+
+    trace = [{"id": r, "arrival_s": 0.0, "n_sys": 20, "n": n, "integrator": 1, "t_end": 30 * HDT, "seed": 3000 + r}
+             for r, n in enumerate([3, 4, 6, 7])]
+    ens_list = [ics.request_ensemble(q) for q in trace]
+    one_pool = 32 * (7 * 7 + 2) * 8 + 2 * 4 * 32  # the largest of these pools (n = 7, 32 slots)
+    with SV.Server(slots_per_pool=32, quantum_steps=10, device_bytes=one_pool) as sv:
+        out = SV.replay(sv, trace, ens_list, collect=True)
+        st = sv.stats()
+    assert st["completed"] == 4 and st["device_bytes"] <= one_pool
+    check_same(trace, ens_list, out)
+
+
+def test_stopped_systems_retire_with_their_request():
+    from paper_1208_1157_gb300 import server as SV
+
+    q = {"id": 0, "arrival_s": 0.0, "n_sys": 10, "n": 3, "integrator": 1, "t_end": 4000 * HDT, "seed": 4000}
+    e = ics.three_body(10, seed=4)
+    e["pos"][3 * 6 + 2] = [98.0, 0.0, 0.0]
+    e["vel"][3 * 6 + 2] = [2.0, 0.0, 0.0]
+    with SV.Server(slots_per_pool=64, quantum_steps=500) as sv:
+        out = SV.replay(sv, [q], [e], collect=True)
+    res = out["done"][0]
+    assert res["status"][6] == 3 and np.all(np.delete(res["status"], 6) == 1)
+    check_same([q], [e], out)
