@@ -198,9 +198,10 @@ def secondary(S, torch, stream):
 
     out = {}
 
-    def timed(ens, t_end, integ, dt, mapping=0, ce=3.0, ej=100.0):
+    def timed(ens, t_end, integ, dt, mapping=0, ce=3.0, ej=100.0, ctas=0):
         with S.Ensemble(ens, stream=stream) as e:
             e.set_option(S.OPT_MAPPING, mapping)
+            e.set_option(S.OPT_CTAS_PER_SM, ctas)
             e.set_stop(ce, ej)
             e.integrate(min(t_end, 2 * dt), integ, dt)  # warm-up (tuner, caches)
             e.set_state(ens["pos"], ens["vel"], time=[0.0] * len(ens["n_body"]),
@@ -220,13 +221,30 @@ def secondary(S, torch, stream):
     out["c2_persistent_500"] = timed(c2, 500 * DT, S.HERMITE4, DT)
     out["c2_persistent_body_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_BODY_PER_LANE)
     out["c2_persistent_system_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE)
+    out["c2_persistent_system_per_lane_3cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE,
+                                                          ctas=3)
     c3 = ics.ragged(65536, seed=3)
+    out["c3_ragged_hermite_per_bin_launches_4_steps"] = timed_per_bin(S, stream, c3, 4 * DT, DT)
     out["c3_ragged_hermite_single_launch_4_steps"] = timed(c3, 4 * DT, S.HERMITE4, DT)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
     out["c4_mvs_dh_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20)
     out["serving"] = serving(S, stream)
     return out
+
+
+def timed_per_bin(S, stream, ens, t_end, dt):
+    """The ragged ensemble with one single-bin launch per body count (no shared work list)."""
+    with S.Ensemble(ens, stream=stream) as e:
+        e.set_option(S.OPT_SINGLE_LAUNCH, 0)
+        e.integrate(2 * dt, S.HERMITE4, dt)
+        e.set_state(ens["pos"], ens["vel"], time=[0.0] * len(ens["n_body"]), status=[0] * len(ens["n_body"]))
+        e.integrate(t_end, S.HERMITE4, dt)
+        st = e.stats()
+    sec = st["kernel_ms"] * 1e-3
+    return {"system_steps_per_s": st["system_steps"] / sec, "pair_interactions_per_s": st["pair_evaluations"] / sec,
+            "kernel_ms": st["kernel_ms"], "launches": st["kernel_launches"], "system_steps": st["system_steps"],
+            "kepler_iterations": 0}
 
 
 def serving(S, stream, n_req=512, rate=200.0, scales=(2000.0, 1000.0), quantum=200):
@@ -368,7 +386,7 @@ def run_ours(args):
     launch_ms = statistics.mean(kernel_ms)
     flops_per_launch = fl * steps_done / args.steps
     achieved = flops_per_launch / (launch_ms * 1e-3)
-    traffic = traffic_per_launch("hermite_persistent_kernel", N_SYS)
+    traffic = traffic_per_launch("hermite_uniform_kernel", N_SYS)
     sec_out = {}
     if rank == 0 and not args.no_secondary:
         sec_out = secondary(S, torch, stream)
@@ -387,7 +405,7 @@ def run_ours(args):
         "pair_interactions_per_s": pairs_total / sec,
         "fp64_flops_per_system_step": fl,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "hermite_persistent_kernel",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "hermite_uniform_kernel<system per lane, n=3>",
                      "peak_kind": "measured DFMA-chain peak on this GPU (2 flops per DFMA)",
                      "avg_launch_ms": launch_ms},
         "e2e": {"value": e2e_steps / e2e_wall, "unit": "system-steps/s", "h2d_bytes_per_step": bytes_io,

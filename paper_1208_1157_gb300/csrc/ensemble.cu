@@ -302,7 +302,7 @@ extern "C" int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const
   CKC(cudaMalloc(&e->d_stage, sizeof(double) * (7 * e->n_bodies + 5 * (size_t)n_sys)));
   CKC(cudaMalloc(&e->d_stage_status, sizeof(int32_t) * n_sys));
   CKC(cudaMalloc(&e->d_counters, sizeof(unsigned long long) * 4));
-  CKC(cudaMalloc(&e->d_work_next, sizeof(int) * 4));
+  CKC(cudaMalloc(&e->d_work_next, sizeof(int) * 32));
   CKC(cudaEventCreate(&e->ev0));
   CKC(cudaEventCreate(&e->ev1));
   CKC(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
@@ -499,13 +499,18 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
     CK(cudaMemcpyAsync(&nmax, W.max_steps, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (e->steps_per_launch > 0 && nmax > 0) {
-      // the per-step launches, captured once per (bin, step count) and replayed
+      // the per-step launches, captured once per (bin, step count) and replayed; the end
+      // time is read from device memory so that a replay serves any t_end
+      const double te = P.t_end;
+      CK(cudaMemcpyAsync(e->d_tend, &te, sizeof(double), cudaMemcpyHostToDevice, st));
+      StepParams PG = P;
+      PG.t_end_dev = e->d_tend;
       std::vector<double> key = {1.0, (double)b.n, (double)b.S, (double)nmax, P.dt, (double)P.n_corr, P.ce_factor,
                                  P.eject2, (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)b.x,
                                  (double)(uintptr_t)W.a0};
       BinView bv = b.view();
       int rc2 = replay_graph(e, key, [&](cudaStream_t cs) -> int {
-        for (int k = 1; k <= nmax; k++) CK(launch_plain(bv, P, W, k, cs));
+        for (int k = 1; k <= nmax; k++) CK(launch_plain(bv, PG, W, k, cs));
         return SWARM_OK;
       });
       if (rc2) return rc2;
@@ -521,7 +526,7 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
 }
 
 static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator) {
-  std::vector<int> maps(e->bins.size());
+  std::vector<int> maps(e->bins.size()), bin_ctas(e->bins.size(), e->ctas_per_sm);
   int ctas = e->ctas_per_sm;
   for (size_t i = 0; i < e->bins.size(); i++) {
     int m = e->mapping;
@@ -531,6 +536,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       if (rc) return rc;
       m = mm;
       if (!ctas && cc) ctas = cc;
+      if (!e->ctas_per_sm) bin_ctas[i] = cc;
     }
     if (m == SWARM_MAP_SYSTEM_PER_LANE && (integrator != SWARM_HERMITE4 || e->bins[i].n > 4))
       m = SWARM_MAP_BODY_PER_LANE;
@@ -538,22 +544,62 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   }
   int rc = build_work(e, maps);
   if (rc) return rc;
-  int maxb = integrator == SWARM_HERMITE4 ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
-  if (maxb <= 0) return fail(SWARM_ECUDA, "persistent kernel cannot be resident");
-  if (!ctas || ctas > maxb) ctas = maxb;
-  int grid = sm_count() * ctas;
-  int need = (e->nwork + 3) / 4;
-  if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
+  // one launch over every bin (the cost-ordered work list), or one single-bin kernel per bin
+  // (body inlined, registers sized for that n) when there is one bin or the option asks
+  const bool per_bin = e->bins.size() == 1 || !e->single_launch;
+  const int sms = sm_count();
+  struct Uni {
+    BinView view;
+    int nunits, grid, mapping, variant;
+  };
+  std::vector<Uni> uni;
+  int grid = 0;
+  if (per_bin) {
+    for (size_t i = 0; i < e->bins.size(); i++) {
+      Uni u;
+      u.view = e->bins[i].view();
+      u.mapping = maps[i];
+      u.nunits = units_of(u.view.n, u.view.S, u.mapping);
+      int blocks = 0;
+      u.variant = bin_ctas[i] == 3 ? 1 : 0;
+      if (integrator == SWARM_HERMITE4) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
+      else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, P, 0, e->stream, &blocks));
+      if (blocks <= 0) return fail(SWARM_ECUDA, "single-bin kernel cannot be resident");
+      int c = (bin_ctas[i] && bin_ctas[i] < blocks) ? bin_ctas[i] : blocks;
+      u.grid = std::max(1, std::min(sms * c, (u.nunits + 3) / 4));
+      uni.push_back(u);
+    }
+  } else {
+    int maxb = integrator == SWARM_HERMITE4 ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
+    if (maxb <= 0) return fail(SWARM_ECUDA, "persistent kernel cannot be resident");
+    if (!ctas || ctas > maxb) ctas = maxb;
+    grid = std::max(1, std::min(sms * ctas, (e->nwork + 3) / 4));
+  }
+  auto enqueue = [&](cudaStream_t cs, const StepParams &Q) -> int {
+    if (per_bin) {
+      for (size_t i = 0; i < uni.size(); i++) {
+        StepParams Qi = Q;
+        Qi.work_next = e->d_work_next + i;
+        CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), cs));
+        if (integrator == SWARM_HERMITE4)
+          CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr, uni[i].variant));
+        else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr));
+      }
+    } else {
+      CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
+      if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+      else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+    }
+    return SWARM_OK;
+  };
+  const int per_call = per_bin ? (int)uni.size() : 1;
   if (e->steps_per_launch <= 0) {
-    CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), e->stream));
-    if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
-    else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, P, grid, e->stream));
-    e->launches++;
+    if ((rc = enqueue(e->stream, P))) return rc;
+    e->launches += per_call;
     return SWARM_OK;
   }
-  // Chunked: K launches of at most L steps each, all with identical parameters (the end
-  // time is read from device memory), captured into one CUDA graph and replayed.
+  // Chunked: K rounds of launches of at most L steps each, all with identical parameters
+  // (the end time is read from device memory), captured into one CUDA graph and replayed.
   const int L = e->steps_per_launch;
   const double span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
   const long long nmax = (long long)std::ceil(span - 1e-9);
@@ -564,18 +610,19 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   const double te = P.t_end;
   CK(cudaMemcpyAsync(e->d_tend, &te, sizeof(double), cudaMemcpyHostToDevice, e->stream));
   std::vector<double> key = {2.0, (double)K, (double)L, (double)integrator, (double)grid, (double)e->nwork, P.dt,
-                             (double)P.n_corr, P.ce_factor, P.eject2, (double)P.log_interval, (double)P.log_cap};
+                             (double)P.n_corr, P.ce_factor, P.eject2, (double)P.log_interval, (double)P.log_cap,
+                             (double)per_bin};
   for (int m : maps) key.push_back((double)m);
+  for (auto &u : uni) key.push_back((double)u.grid);
   rc = replay_graph(e, key, [&](cudaStream_t cs) -> int {
     for (int k = 0; k < K; k++) {
-      CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
-      if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
-      else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+      int r2 = enqueue(cs, Q);
+      if (r2) return r2;
     }
     return SWARM_OK;
   });
   if (rc) return rc;
-  e->launches += K;
+  e->launches += (int64_t)K * per_call;
   return SWARM_OK;
 }
 

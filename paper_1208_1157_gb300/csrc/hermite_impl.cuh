@@ -9,7 +9,7 @@ namespace swarm {
 // ---------------------------------------------------------------- body per lane
 // One work unit = one warp's G = 32/N systems of a bin, integrated for the whole call.
 template <int N>
-__device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+__device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepParams &P, int unit) {
   using R = Ring<N>;
   constexpr int G = R::G;
   constexpr int RT = R::RT > 0 ? R::RT : 1;
@@ -117,8 +117,8 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
     const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
     const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
     const int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-    const double tk = step_time(plan, k, t0, P.dt);
     if (active && code) {
+      const double tk = step_time(plan, k, t0, P.dt);
       if (sys_ok) {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -135,7 +135,7 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
       double e[4];
       ring_energy<N>(x, v, m, b, base, e);
-      if (active && !code && b == 0 && sys_ok) write_log(P, B.gidx[s], tk, e);
+      if (active && !code && b == 0 && sys_ok) write_log(P, B.gidx[s], step_time(plan, k, t0, P.dt), e);
     }
   }
   if (alive && sys_ok) {
@@ -160,7 +160,7 @@ __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams
 
 // ---------------------------------------------------------------- system per lane
 template <int N>
-__device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+__device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepParams &P, int unit) {
   const int s = unit * 32 + (threadIdx.x & 31);
   if (s >= B.S) return;
   const int SP = B.S_pad;
@@ -194,7 +194,7 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
   const HCoef clast = hcoef(plan.h_last);
   int steps_done = 0;
   int code = 0;
-  double tk = t0;
+  const bool ej_on = P.eject2 > 0.0;
   for (int k = 1; k <= Ns; k++) {
     const HCoef C = (k == Ns && !plan.exact) ? clast : cdt;
     double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
@@ -227,14 +227,13 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
         v[i][c] = vk[i][c];
       }
     steps_done = k;
-    tk = step_time(plan, k, t0, P.dt);
     bool nf = false, ej = false, ce = false;
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
 #pragma unroll
-    for (int i = 1; i < N; i++) ej |= (P.eject2 > 0.0) && (q2[i] > P.eject2);
+    for (int i = 1; i < N; i++) ej |= ej_on && (q2[i] > P.eject2);
 #pragma unroll
     for (int i = 1; i < N; i++)
 #pragma unroll
@@ -245,9 +244,10 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
       double e[4];
       spl_energy<N>(x, v, m, e);
-      write_log(P, B.gidx[s], tk, e);
+      write_log(P, B.gidx[s], step_time(plan, k, t0, P.dt), e);
     }
   }
+  const double tk = step_time(plan, steps_done, t0, P.dt);
 #pragma unroll
   for (int i = 0; i < N; i++)
 #pragma unroll
@@ -262,6 +262,44 @@ __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams
     atomicAdd(&P.counters[0], (unsigned long long)steps_done);
     atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done * (P.n_corr + 1)));
   }
+}
+
+// Out-of-line copies called by the multi-body-count dispatcher kernel.
+template <int N>
+__device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+  bpl_hermite_body<N>(B, P, unit);
+}
+template <int N>
+__device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
+  spl_hermite_body<N>(B, P, unit);
+}
+
+// Persistent kernel for one bin (one body count, one mapping): the unit body is inlined,
+// so registers are allocated for this n alone.  Warps pull unit indices from a counter.
+// MINB = 3 is the high-occupancy variant (registers capped for 3 CTAs of 128 threads per SM).
+template <int MAP, int N, int MINB>
+__global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, int nunits, StepParams P) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(P.work_next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nunits) break;
+    if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_body<N>(B, P, w);
+    else bpl_hermite_body<N>(B, P, w);
+  }
+}
+
+template <int MAP, int N, int MINB = 2>
+cudaError_t launch_hermite_uniform_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st) {
+  hermite_uniform_kernel<MAP, N, MINB><<<grid, 128, 0, st>>>(B, nunits, P);
+  return cudaGetLastError();
+}
+template <int MAP, int N, int MINB = 2>
+int hermite_uniform_blocks_n() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_uniform_kernel<MAP, N, MINB>, 128, 0);
+  return nb;
 }
 
 }  // namespace swarm

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(128) plain_step_kernel(BinView B, StepParams P
       if (kc > 0.0 && close_encounter(d2[i][k2], kc, q2[i], q2[k2])) ce = true;
     }
   const int code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-  const double tk = (k == Ns) ? P.t_end : W.t0[s] + (double)k * P.dt;
+  const double te = P.t_end_dev ? *P.t_end_dev : P.t_end;  // device copy when replayed from a graph
+  const double tk = (k == Ns) ? te : W.t0[s] + (double)k * P.dt;
 #pragma unroll
   for (int i = 0; i < N; i++)
 #pragma unroll
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(128) plain_step_kernel(BinView B, StepParams P
     B.t[s] = tk;
     B.status[s] = code;
   } else if (k == Ns) {
-    B.t[s] = P.t_end;
+    B.t[s] = te;
     B.status[s] = SWARM_SYS_DONE;
   }
   if (!code && P.log_interval > 0 && (k % P.log_interval) == 0) {
@@ -183,6 +184,21 @@ cudaError_t launch_hermite_persistent(const BinView *d_bins, const int4 *d_work,
                                       int grid, cudaStream_t st) {
   hermite_persistent_kernel<<<grid, 128, 0, st>>>(d_bins, d_work, nwork, P);
   return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_uniform_spl(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                       cudaStream_t st, int *blocks, int variant);
+cudaError_t launch_hermite_uniform_bpl_a(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                         cudaStream_t st, int *blocks);
+cudaError_t launch_hermite_uniform_bpl_b(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                         cudaStream_t st, int *blocks);
+
+cudaError_t launch_hermite_uniform(int mapping, const BinView &B, int nunits, const StepParams &P, int grid,
+                                   cudaStream_t st, int *blocks, int variant) {
+  if (mapping == SWARM_MAP_SYSTEM_PER_LANE)
+    return launch_hermite_uniform_spl(B.n, B, nunits, P, grid, st, blocks, variant);
+  if (B.n <= 8) return launch_hermite_uniform_bpl_a(B.n, B, nunits, P, grid, st, blocks);
+  return launch_hermite_uniform_bpl_b(B.n, B, nunits, P, grid, st, blocks);
 }
 
 int hermite_persistent_max_blocks_per_sm() {

@@ -25,6 +25,13 @@ cudaError_t launch_mvs_persistent(const BinView *d_bins, const int4 *d_work, int
                                   int grid, cudaStream_t st);
 int mvs_persistent_max_blocks_per_sm();
 
+// Single-bin persistent kernels (unit body inlined).  grid <= 0 only reports the
+// resident blocks per SM in *blocks.  variant 1: high-occupancy build where one exists.
+cudaError_t launch_hermite_uniform(int mapping, const BinView &B, int nunits, const StepParams &P, int grid,
+                                   cudaStream_t st, int *blocks, int variant = 0);
+cudaError_t launch_mvs_uniform(bool jacobi, const BinView &B, int nunits, const StepParams &P, int grid,
+                               cudaStream_t st, int *blocks);
+
 void set_last_error(const char *msg);
 
 cudaError_t launch_fp64_peak(double *out, long long iters, int grid, int block, cudaStream_t st);

@@ -350,7 +350,7 @@ __device__ __forceinline__ void mvs_acc(const double (&q)[3], double m, double w
 
 // ---------------------------------------------------------------- one work unit
 template <int N, bool JAC>
-__device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P, int unit) {
+__device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams &P, int unit) {
   constexpr int G = 32 / N;
   constexpr int MR = JAC ? N : N - 1;  // members of the acceleration ring
   constexpr int RTA = ARing<MR>::RTA;
@@ -556,6 +556,36 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
       atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done));
     }
   }
+}
+
+template <int N, bool JAC>
+__device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P, int unit) {
+  bpl_mvs_body<N, JAC>(B, P, unit);
+}
+
+// Persistent kernel for one bin (see hermite_uniform_kernel).
+template <int N, bool JAC>
+__global__ void __launch_bounds__(128, 2) mvs_uniform_kernel(BinView B, int nunits, StepParams P) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(P.work_next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nunits) break;
+    bpl_mvs_body<N, JAC>(B, P, w);
+  }
+}
+
+template <int N, bool JAC>
+cudaError_t launch_mvs_uniform_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st) {
+  mvs_uniform_kernel<N, JAC><<<grid, 128, 0, st>>>(B, nunits, P);
+  return cudaGetLastError();
+}
+template <int N, bool JAC>
+int mvs_uniform_blocks_n() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mvs_uniform_kernel<N, JAC>, 128, 0);
+  return nb;
 }
 
 }  // namespace swarm

@@ -51,6 +51,23 @@ cudaError_t launch_mvs_persistent(const BinView *d_bins, const int4 *d_work, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_mvs_uniform_dh_a(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                    cudaStream_t st, int *blocks);
+cudaError_t launch_mvs_uniform_dh_b(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                    cudaStream_t st, int *blocks);
+cudaError_t launch_mvs_uniform_jac_a(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                     cudaStream_t st, int *blocks);
+cudaError_t launch_mvs_uniform_jac_b(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                     cudaStream_t st, int *blocks);
+
+cudaError_t launch_mvs_uniform(bool jacobi, const BinView &B, int nunits, const StepParams &P, int grid,
+                               cudaStream_t st, int *blocks) {
+  if (jacobi) return B.n <= 8 ? launch_mvs_uniform_jac_a(B.n, B, nunits, P, grid, st, blocks)
+                              : launch_mvs_uniform_jac_b(B.n, B, nunits, P, grid, st, blocks);
+  return B.n <= 8 ? launch_mvs_uniform_dh_a(B.n, B, nunits, P, grid, st, blocks)
+                  : launch_mvs_uniform_dh_b(B.n, B, nunits, P, grid, st, blocks);
+}
+
 int mvs_persistent_max_blocks_per_sm() {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mvs_persistent_kernel, 128, 0);

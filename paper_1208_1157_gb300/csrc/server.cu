@@ -16,6 +16,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -42,11 +43,13 @@ int sfail(int rc, const std::string &m) {
 
 struct Pool {
   int integ = 0, n = 0, cap = 0;
+  int mapping = SWARM_MAP_BODY_PER_LANE, per = 1;  // thread mapping, systems per work unit
   void *block = nullptr;
   BinView view{};
   double *t_end = nullptr;
-  std::vector<int> free_slots;
+  std::set<int> free_slots;    // lowest slots are handed out first (dense work units)
   std::vector<int64_t> owner;  // request id per slot, -1 if free
+  std::vector<int> unit_occ;   // occupied slots per work unit
   size_t bytes = 0;
 };
 
@@ -182,9 +185,15 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
   SCK(cudaMemsetAsync(p->block, 0, bytes, sv->stream));
   fill_status_kernel<<<(cap + 255) / 256, 256, 0, sv->stream>>>(p->view.status, cap, kFree);
   SCK(cudaGetLastError());
-  p->free_slots.resize(cap);
-  for (int i = 0; i < cap; i++) p->free_slots[i] = cap - 1 - i;  // pop_back gives 0, 1, 2, ...
+  for (int i = 0; i < cap; i++) p->free_slots.insert(p->free_slots.end(), i);
   p->owner.assign(cap, -1);
+  int32_t mapping = SWARM_MAP_BODY_PER_LANE, ctas = 0;
+  int rc = tuner_choice_internal(n, integ, cap, sv->stream, &mapping, &ctas);
+  if (rc) return rc;
+  if (integ != SWARM_HERMITE4 || n > 4) mapping = SWARM_MAP_BODY_PER_LANE;
+  p->mapping = mapping;
+  p->per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : 32 / n;
+  p->unit_occ.assign((cap + p->per - 1) / p->per, 0);
   sv->bytes_used += bytes;
   sv->launch[integ].dirty = true;
   *out = p.get();
@@ -194,41 +203,42 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
 
 static int rebuild_launch(swarm_server *sv, int integ) {
   auto &L = sv->launch[integ];
-  if (!L.dirty) return SWARM_OK;
-  std::vector<BinView> views;
+  std::vector<Pool *> pools;
+  for (auto &kv : sv->pools)
+    if (kv.second->integ == integ) pools.push_back(kv.second.get());
+  if (L.dirty) {
+    std::vector<BinView> views;
+    for (Pool *p : pools) views.push_back(p->view);
+    if ((int)views.size() > L.cap_bins) {
+      if (L.d_bins) cudaFree(L.d_bins);
+      L.d_bins = nullptr;
+      SCK(cudaMalloc(&L.d_bins, sizeof(BinView) * std::max<size_t>(views.size(), 16)));
+      L.cap_bins = (int)std::max<size_t>(views.size(), 16);
+    }
+    if (!L.d_next) SCK(cudaMalloc(&L.d_next, sizeof(int)));
+    if (!views.empty())
+      SCK(cudaMemcpyAsync(L.d_bins, views.data(), sizeof(BinView) * views.size(), cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaStreamSynchronize(sv->stream));
+    L.nbins = (int)views.size();
+    L.dirty = false;
+  }
+  // only the work units that hold an occupied slot, heaviest body count first
   std::vector<int4> work;
-  for (auto &kv : sv->pools) {
-    Pool *p = kv.second.get();
-    if (p->integ != integ) continue;
-    int32_t mapping = SWARM_MAP_BODY_PER_LANE, ctas = 0;
-    int rc = tuner_choice_internal(p->n, integ, p->cap, sv->stream, &mapping, &ctas);
-    if (rc) return rc;
-    if (integ != SWARM_HERMITE4 || p->n > 4) mapping = SWARM_MAP_BODY_PER_LANE;
-    const int per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : 32 / p->n;
-    const int units = (p->cap + per - 1) / per;
-    for (int u = 0; u < units; u++) work.push_back(make_int4((int)views.size(), u, mapping, p->n));
-    views.push_back(p->view);
+  for (size_t b = 0; b < pools.size(); b++) {
+    Pool *p = pools[b];
+    for (int u = 0; u < (int)p->unit_occ.size(); u++)
+      if (p->unit_occ[u]) work.push_back(make_int4((int)b, u, p->mapping, p->n));
   }
   std::stable_sort(work.begin(), work.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
-  if ((int)views.size() > L.cap_bins) {
-    if (L.d_bins) cudaFree(L.d_bins);
-    L.d_bins = nullptr;
-    SCK(cudaMalloc(&L.d_bins, sizeof(BinView) * std::max<size_t>(views.size(), 16)));
-    L.cap_bins = (int)std::max<size_t>(views.size(), 16);
-  }
   if ((int)work.size() > L.cap_work) {
     if (L.d_work) cudaFree(L.d_work);
     L.d_work = nullptr;
     SCK(cudaMalloc(&L.d_work, sizeof(int4) * work.size()));
     L.cap_work = (int)work.size();
   }
-  if (!L.d_next) SCK(cudaMalloc(&L.d_next, sizeof(int)));
-  if (!views.empty()) SCK(cudaMemcpyAsync(L.d_bins, views.data(), sizeof(BinView) * views.size(), cudaMemcpyHostToDevice, sv->stream));
-  if (!work.empty()) SCK(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, sv->stream));
-  SCK(cudaStreamSynchronize(sv->stream));  // host vectors go out of scope
+  if (!work.empty())
+    SCK(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, sv->stream));
   L.nwork = (int)work.size();
-  L.nbins = (int)views.size();
-  L.dirty = false;
   return SWARM_OK;
 }
 
@@ -314,9 +324,11 @@ static int admit(swarm_server *sv) {
     }
     r->slots.resize(r->n_sys);
     for (int i = 0; i < r->n_sys; i++) {
-      r->slots[i] = p->free_slots.back();
-      p->free_slots.pop_back();
-      p->owner[r->slots[i]] = r->id;
+      const int slot = *p->free_slots.begin();
+      p->free_slots.erase(p->free_slots.begin());
+      r->slots[i] = slot;
+      p->owner[slot] = r->id;
+      p->unit_occ[slot / p->per]++;
     }
     r->pool = p;
     const size_t nb = (size_t)r->n_sys * r->n;
@@ -381,7 +393,8 @@ static int retire(swarm_server *sv, int32_t *n_completed) {
     SCK(cudaStreamSynchronize(sv->stream));
     for (int s : r->slots) {
       p->owner[s] = -1;
-      p->free_slots.push_back(s);
+      p->free_slots.insert(s);
+      p->unit_occ[s / p->per]--;
     }
     r->slots.clear();
     r->state = SWARM_REQ_DONE;
@@ -407,6 +420,7 @@ extern "C" int swarm_server_step(swarm_server *sv, int32_t *n_completed) {
     if (!occupied) continue;
     if ((rc = rebuild_launch(sv, integ))) return rc;
     auto &L = sv->launch[integ];
+    if (L.nwork == 0) continue;
     StepParams P{};
     P.t_end = 0;
     P.dt = integ == SWARM_HERMITE4 ? sv->cfg.hermite_dt : sv->cfg.mvs_dt;

@@ -99,11 +99,14 @@ int tuner_choice_internal(int n, int integrator, int S, cudaStream_t st, int32_t
     // fixed rule: a whole system per lane for the smallest systems in large ensembles
     if (integrator == SWARM_HERMITE4 && n <= 3 && S >= 16384) c.mapping = SWARM_MAP_SYSTEM_PER_LANE;
   } else {
-    int probeS = S < 65536 ? S : 65536;
+    // probe at the bin's own size: how the work units spread over the SM sub-partitions
+    // (granularity) decides between the mappings as much as the per-step cost does
+    int probeS = S < (1 << 20) ? S : (1 << 20);
     std::vector<Choice> cands = {{SWARM_MAP_BODY_PER_LANE, 0}, {SWARM_MAP_BODY_PER_LANE, 1}};
     if (integrator == SWARM_HERMITE4 && n <= 4) {
       cands.push_back({SWARM_MAP_SYSTEM_PER_LANE, 0});
-      cands.push_back({SWARM_MAP_SYSTEM_PER_LANE, 1});
+      // 3 CTAs per SM selects the high-occupancy build (n <= 3)
+      if (n <= 3) cands.push_back({SWARM_MAP_SYSTEM_PER_LANE, 3});
     }
     double best = -1;
     for (auto &cd : cands) {
