@@ -45,9 +45,13 @@ enum swarm_rc {
 };
 
 enum swarm_integrator {
-  SWARM_HERMITE4 = 1,   /* Sec. 2.2.1 / Algorithm 2 */
-  SWARM_MVS_DH = 2,     /* Sec. 2.2.3, democratic heliocentric, five sub-steps */
-  SWARM_MVS_JACOBI = 3  /* Wisdom & Holman 1991 map in Jacobi coordinates */
+  SWARM_HERMITE4 = 1,          /* Sec. 2.2.1 / Algorithm 2 */
+  SWARM_MVS_DH = 2,            /* Sec. 2.2.3, democratic heliocentric, five sub-steps */
+  SWARM_MVS_JACOBI = 3,        /* Wisdom & Holman 1991 map in Jacobi coordinates */
+  SWARM_HERMITE4_ADAPTIVE = 4  /* Hermite with the step of Eq. 5, dt = tau (sum |j|^2/|a|^2)^(-1/2) from
+                                  the start of each step; swarm_integrate's dt is tau (its sign is the
+                                  direction); the last step lands on t_end; at most 2^24 steps per call
+                                  and system (a system short of t_end then stays ACTIVE) */
 };
 
 /* per-system status (the monitor of Sec. 4.3, Algorithm 1) */
@@ -79,7 +83,10 @@ enum swarm_option {
                                     this many steps, replayed from a captured CUDA graph */
   SWARM_OPT_SINGLE_LAUNCH = 6,  /* 1 (default): all n-bins share one persistent launch with a
                                     cost-ordered work list; 0: one launch per bin */
-  SWARM_OPT_CTAS_PER_SM = 7     /* persistent grid size per SM (0 = tuner/default) */
+  SWARM_OPT_CTAS_PER_SM = 7,    /* persistent grid size per SM (0 = tuner/default) */
+  SWARM_OPT_CORRECTOR = 8       /* Hermite corrector: 0 = time-symmetric form of Kokubo et al. 1998
+                                   (default); 1 = the printed Eq. 4 read with 3/20 and the predicted
+                                   base (same velocity update, 4th order, not time-symmetric) */
 };
 
 typedef struct swarm_ensemble swarm_ensemble;
@@ -165,8 +172,9 @@ typedef struct {
   int64_t occupied_slots, pool_slots, device_bytes;
   int64_t quanta, system_steps, pair_evaluations;
   double kernel_ms;
+  int64_t cancelled;
 } swarm_server_stats;
-enum swarm_request_state { SWARM_REQ_QUEUED = 0, SWARM_REQ_RUNNING = 1, SWARM_REQ_DONE = 2 };
+enum swarm_request_state { SWARM_REQ_QUEUED = 0, SWARM_REQ_RUNNING = 1, SWARM_REQ_DONE = 2, SWARM_REQ_CANCELLED = 3 };
 
 int swarm_server_create(const swarm_server_config *cfg, void *cuda_stream, swarm_server **out);
 /* Host arrays in the creation layout ([n_sys*n_body][3]); copied, so the caller may reuse
@@ -179,7 +187,10 @@ int swarm_server_step(swarm_server *sv, int32_t *n_completed);
  * NULL) and its latency (submit to retirement, seconds). */
 int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, double *pos, double *vel, double *time,
                       int32_t *status, double *latency_s);
-/* Forget a finished request (frees its host copy of the results). */
+/* Cancel a queued or running request (its slots are freed for the next admissions);
+ * SWARM_ESTATE if it already finished. */
+int swarm_server_cancel(swarm_server *sv, int64_t id);
+/* Forget a finished or cancelled request (frees its host copy of the results). */
 int swarm_server_release(swarm_server *sv, int64_t id);
 int swarm_server_query(const swarm_server *sv, swarm_server_stats *out);
 void swarm_server_destroy(swarm_server *sv);

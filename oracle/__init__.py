@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE = range(6)
-HERMITE, MVS_DH, MVS_JACOBI = 1, 2, 3
+HERMITE, MVS_DH, MVS_JACOBI, HERMITE_ADAPTIVE = 1, 2, 3, 4
 CORR_KOKUBO, CORR_PRINTED = 0, 1
 
 _lock = threading.Lock()
@@ -60,6 +60,8 @@ def _declare(L):
     L.or_acc.argtypes = [C.c_int, _dp, _dp, _dp]
     L.or_hermite_step.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_int, C.c_int]
     L.or_energy.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.or_adaptive_dt.argtypes = [C.c_int, _dp, _dp, C.c_double]
+    L.or_adaptive_dt.restype = C.c_double
     L.or_monitor.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, C.c_double]
     L.or_monitor.restype = C.c_int
     L.or_stumpff.argtypes = [C.c_double, _dp, _dp]
@@ -107,6 +109,11 @@ def hermite_step(m, x, v, a0, j0, dt, n_corr=2, form=CORR_KOKUBO):
     m, x, v, a0, j0 = _f64(m), _f64(x, (-1, 3)), _f64(v, (-1, 3)), _f64(a0, (-1, 3)), _f64(j0, (-1, 3))
     lib().or_hermite_step(len(m), _d(m), _d(x), _d(v), _d(a0), _d(j0), float(dt), int(n_corr), int(form))
     return x, v, a0, j0
+
+
+def adaptive_dt(a0, j0, tau):
+    a0, j0 = _f64(a0, (-1, 3)), _f64(j0, (-1, 3))
+    return float(lib().or_adaptive_dt(len(a0), _d(a0), _d(j0), float(tau)))
 
 
 def energy(m, x, v):

@@ -108,6 +108,16 @@ void or_hermite_step(int n, const double *m, double *x, double *v, double *a0, d
   or_accjerk(n, m, x, v, a0, j0);
 }
 
+/* Eq. 5 (Sec. 4.3.2, "Time Step adaptation"). */
+double or_adaptive_dt(int n, const double *a0, const double *j0, double tau) {
+  double s = 0.0;
+  for (int i = 0; i < n; i++) {
+    const double *a = a0 + 3 * i, *j = j0 + 3 * i;
+    s += dot3(j, j) / dot3(a, a);
+  }
+  return tau / sqrt(s);
+}
+
 /* Eq. 6 with each pair once; L = sum m x cross v. */
 void or_energy(int n, const double *m, const double *x, const double *v, double *E, double *L) {
   double kin = 0, pot = 0;
@@ -428,6 +438,57 @@ int or_integrate(int n, const double *m, double *x, double *v, double *t, int *s
                  long long *kepler_iters) {
   if (n < 2 || n > MAXN || dt == 0.0 || !isfinite(dt)) return -1;
   if (*status >= OR_CLOSE_ENCOUNTER) return 0;
+  if (p->integrator == OR_HERMITE_ADAPTIVE) {
+    /* dt is tau; steps of min(Eq. 5, remaining time) toward t_end */
+    const double tau = fabs(dt);
+    const double dir = dt > 0 ? 1.0 : -1.0;
+    double rem = (t_end - *t) * dir;
+    if (!(rem > 1e-12 * fmax(1.0, fabs(t_end)))) {
+      *status = OR_DONE;
+      return 0;
+    }
+    double a0[3 * MAXN], j0[3 * MAXN];
+    or_accjerk(n, m, x, v, a0, j0);
+    int nlog = log_count ? *log_count : 0;
+    for (long long k = 1; k <= 16777216LL; k++) {
+      double h = or_adaptive_dt(n, a0, j0, tau);
+      if (!(h > 0) || !isfinite(h)) {
+        *status = OR_NONFINITE;
+        if (log_count) *log_count = nlog;
+        return 0;
+      }
+      rem = (t_end - *t) * dir;
+      int last = h >= rem;
+      if (last) h = rem;
+      or_hermite_step(n, m, x, v, a0, j0, dir * h, p->n_corr, p->corr_form);
+      *t = last ? t_end : *t + dir * h;
+      int st = or_monitor(n, m, x, v, p->ce_factor, p->eject_radius);
+      if (st != OR_ACTIVE) {
+        *status = st;
+        if (log_count) *log_count = nlog;
+        return 0;
+      }
+      if (p->log_interval > 0 && log && k % p->log_interval == 0 && nlog < p->log_cap) {
+        double E, L[3];
+        or_energy(n, m, x, v, &E, L);
+        double *rec = log + 5 * nlog;
+        rec[0] = *t;
+        rec[1] = E;
+        rec[2] = L[0];
+        rec[3] = L[1];
+        rec[4] = L[2];
+        nlog++;
+      }
+      if (last) {
+        *status = OR_DONE;
+        if (log_count) *log_count = nlog;
+        return 0;
+      }
+    }
+    *status = OR_ACTIVE;  /* step cap reached before t_end */
+    if (log_count) *log_count = nlog;
+    return 0;
+  }
   double D = (t_end - *t) / dt;
   if (!(D > 1e-9)) {
     *status = OR_DONE;

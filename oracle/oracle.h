@@ -21,7 +21,7 @@ extern "C" {
 enum { OR_ACTIVE = 0, OR_DONE = 1, OR_CLOSE_ENCOUNTER = 2, OR_EJECTED = 3,
        OR_KEPLER_NOCONV = 4, OR_NONFINITE = 5 };
 /* integrators */
-enum { OR_HERMITE = 1, OR_MVS_DH = 2, OR_MVS_JACOBI = 3 };
+enum { OR_HERMITE = 1, OR_MVS_DH = 2, OR_MVS_JACOBI = 3, OR_HERMITE_ADAPTIVE = 4 };
 /* Hermite corrector forms: the time-symmetric form of Kokubo et al. 1998 cited in
  * Sec. 2.2.1, and the printed Eq. 4 read with 3/20 and the predicted base. */
 enum { OR_CORR_KOKUBO = 0, OR_CORR_PRINTED = 1 };
@@ -35,6 +35,9 @@ void or_acc(int n, const double *m, const double *x, double *a);
  * the evaluation at the corrected state that gives the next step's a0, j0. */
 void or_hermite_step(int n, const double *m, double *x, double *v, double *a0, double *j0,
                      double dt, int n_corr, int form);
+
+/* Eq. 5: adaptive step tau * (sum_i |j_i|^2 / |a_i|^2)^(-1/2) from a0, j0 (tau > 0). */
+double or_adaptive_dt(int n, const double *a0, const double *j0, double tau);
 
 /* Eq. 6 energy (pairs counted once) and total angular momentum L[3]. */
 void or_energy(int n, const double *m, const double *x, const double *v, double *E, double *L);
@@ -68,9 +71,12 @@ void or_dh_interaction_acc(int n, const double *m, const double *q, double *acc)
 void or_jacobi_interaction_acc(int n, const double *m, const double *r, double *acc);
 
 /* Integrate one system from *t to t_end (Algorithm 1 with a monitor after every
- * step).  Step count: N = round(D) when D = (t_end - t)/dt is within 1e-9 of an
- * integer, else ceil(D) with the last step shortened to land on t_end.  Systems whose
- * status is a stop code (>= 2) are left untouched.  Every log_interval steps (0 = off)
+ * step).  Fixed steps: N = round(D) when D = (t_end - t)/dt is within 1e-9 of an
+ * integer, else ceil(D) with the last step shortened to land on t_end.
+ * OR_HERMITE_ADAPTIVE takes dt as the step-size scale tau of Eq. 5 (its sign gives the
+ * direction): each step is min(Eq. 5 step, distance to t_end), so the last one lands on
+ * t_end; at most 2^24 steps per call, after which the system stays ACTIVE at the time
+ * reached.  Systems whose status is a stop code (>= 2) are left untouched.  Every log_interval steps (0 = off)
  * one record (t, E, Lx, Ly, Lz) is appended to log (capacity log_cap records). */
 typedef struct {
   int integrator, n_corr, corr_form, log_interval, log_cap;

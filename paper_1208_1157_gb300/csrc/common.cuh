@@ -27,6 +27,7 @@ struct BinView {
 struct StepParams {
   double t_end, dt;
   int n_corr;            // Hermite corrector passes
+  int corr_form = 0;     // 0: time-symmetric corrector; 1: printed Eq. 4 form (3/20, predicted base)
   int integrator;
   double ce_factor;      // close-encounter factor in mutual Hill radii (<= 0: off)
   double eject2;         // squared ejection radius (<= 0: off)

@@ -86,6 +86,7 @@ struct swarm_ensemble {
   int64_t plain_cap = 0;
   void *plain_block = nullptr;
   int mapping = SWARM_MAP_AUTO, n_corr = 2, steps_per_launch = 0, single_launch = 1, ctas_per_sm = 0;
+  int corr_form = 0;
   double ce = 0.0, eject = 0.0;
   double t_lo = 0.0, t_hi = 0.0;  // range of runnable systems' times (step-count guard)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -372,6 +373,10 @@ extern "C" int swarm_set_option(swarm_ensemble *e, int option, int64_t value) {
     case SWARM_OPT_SINGLE_LAUNCH:
       e->single_launch = value ? 1 : 0;
       return SWARM_OK;
+    case SWARM_OPT_CORRECTOR:
+      if (value != 0 && value != 1) return fail(SWARM_EINVAL, "corrector form must be 0 or 1");
+      e->corr_form = (int)value;
+      return SWARM_OK;
     case SWARM_OPT_CTAS_PER_SM:
       if (value < 0 || value > 32) return fail(SWARM_EINVAL, "ctas per SM out of range");
       e->ctas_per_sm = (int)value;
@@ -425,6 +430,7 @@ static StepParams make_params(swarm_ensemble *e, double t_end, int integrator, d
   P.t_end = t_end;
   P.dt = dt;
   P.n_corr = e->n_corr;
+  P.corr_form = e->corr_form;
   P.integrator = integrator;
   P.ce_factor = e->ce;
   P.eject2 = e->eject > 0 ? e->eject * e->eject : 0.0;
@@ -525,6 +531,10 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
   return SWARM_OK;
 }
 
+static bool hermite_family(int integrator) {
+  return integrator == SWARM_HERMITE4 || integrator == SWARM_HERMITE4_ADAPTIVE;
+}
+
 static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator) {
   std::vector<int> maps(e->bins.size()), bin_ctas(e->bins.size(), e->ctas_per_sm);
   int ctas = e->ctas_per_sm;
@@ -532,13 +542,15 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     int m = e->mapping;
     if (m == SWARM_MAP_AUTO) {
       int32_t mm = SWARM_MAP_BODY_PER_LANE, cc = 0;
-      int rc = tuner_choice_internal(e->bins[i].n, integrator, e->bins[i].S, e->stream, &mm, &cc);
+      // the adaptive Hermite shares the fixed-step Hermite's tuning (same kernels per step)
+      int rc = tuner_choice_internal(e->bins[i].n, hermite_family(integrator) ? SWARM_HERMITE4 : integrator,
+                                     e->bins[i].S, e->stream, &mm, &cc);
       if (rc) return rc;
       m = mm;
       if (!ctas && cc) ctas = cc;
       if (!e->ctas_per_sm) bin_ctas[i] = cc;
     }
-    if (m == SWARM_MAP_SYSTEM_PER_LANE && (integrator != SWARM_HERMITE4 || e->bins[i].n > 4))
+    if (m == SWARM_MAP_SYSTEM_PER_LANE && (!hermite_family(integrator) || e->bins[i].n > 4))
       m = SWARM_MAP_BODY_PER_LANE;
     maps[i] = m;
   }
@@ -562,7 +574,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = units_of(u.view.n, u.view.S, u.mapping);
       int blocks = 0;
       u.variant = bin_ctas[i] == 3 ? 1 : 0;
-      if (integrator == SWARM_HERMITE4) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
+      if (hermite_family(integrator)) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
       else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, P, 0, e->stream, &blocks));
       if (blocks <= 0) return fail(SWARM_ECUDA, "single-bin kernel cannot be resident");
       int c = (bin_ctas[i] && bin_ctas[i] < blocks) ? bin_ctas[i] : blocks;
@@ -570,7 +582,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       uni.push_back(u);
     }
   } else {
-    int maxb = integrator == SWARM_HERMITE4 ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
+    int maxb = hermite_family(integrator) ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
     if (maxb <= 0) return fail(SWARM_ECUDA, "persistent kernel cannot be resident");
     if (!ctas || ctas > maxb) ctas = maxb;
     grid = std::max(1, std::min(sms * ctas, (e->nwork + 3) / 4));
@@ -581,19 +593,20 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
         StepParams Qi = Q;
         Qi.work_next = e->d_work_next + i;
         CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), cs));
-        if (integrator == SWARM_HERMITE4)
+        if (hermite_family(integrator))
           CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr, uni[i].variant));
         else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr));
       }
     } else {
       CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
-      if (integrator == SWARM_HERMITE4) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+      if (hermite_family(integrator)) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
       else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
     }
     return SWARM_OK;
   };
   const int per_call = per_bin ? (int)uni.size() : 1;
-  if (e->steps_per_launch <= 0) {
+  // the adaptive step count is not known in advance: always one launch per call
+  if (e->steps_per_launch <= 0 || integrator == SWARM_HERMITE4_ADAPTIVE) {
     if ((rc = enqueue(e->stream, P))) return rc;
     e->launches += per_call;
     return SWARM_OK;
@@ -628,13 +641,14 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
 
 static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, double dt, bool sync) {
   if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");
-  if (integrator != SWARM_HERMITE4 && integrator != SWARM_MVS_DH && integrator != SWARM_MVS_JACOBI)
+  if (integrator != SWARM_HERMITE4 && integrator != SWARM_MVS_DH && integrator != SWARM_MVS_JACOBI &&
+      integrator != SWARM_HERMITE4_ADAPTIVE)
     return fail(SWARM_EINVAL, "unknown integrator %d", integrator);
   if (!(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t_end)) return fail(SWARM_EINVAL, "dt must be finite and non-zero, t_end finite");
   double span = std::max(std::fabs(t_end - e->t_lo), std::fabs(t_end - e->t_hi)) / std::fabs(dt);
-  if (span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
-  if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && integrator != SWARM_HERMITE4)
-    return fail(SWARM_EINVAL, "the plain per-step baseline exists for the Hermite integrator only");
+  if (integrator != SWARM_HERMITE4_ADAPTIVE && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
+  if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && (integrator != SWARM_HERMITE4 || e->corr_form))
+    return fail(SWARM_EINVAL, "the plain per-step baseline exists for the fixed-step time-symmetric Hermite only");
   StepParams P = make_params(e, t_end, integrator, dt);
   CK(cudaMemsetAsync(e->d_counters, 0, sizeof(unsigned long long) * 4, e->stream));
   e->launches = 0;
@@ -644,7 +658,12 @@ static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, doubl
   CK(cudaEventRecord(e->ev1, e->stream));
   e->last_integrator = integrator;
   e->stats_pending = true;
-  e->t_lo = e->t_hi = t_end;  // every runnable system ends at t_end (stopped ones never run again)
+  if (integrator != SWARM_HERMITE4_ADAPTIVE) {
+    e->t_lo = e->t_hi = t_end;  // every runnable system ends at t_end (stopped ones never run again)
+  } else {  // an adaptive call may stop short of t_end (step cap)
+    e->t_lo = std::min(e->t_lo, t_end);
+    e->t_hi = std::max(e->t_hi, t_end);
+  }
   if (sync) CK(cudaStreamSynchronize(e->stream));
   return SWARM_OK;
 }

@@ -25,6 +25,21 @@ __device__ __forceinline__ HCoef hcoef(double h) {
   c.h2_12 = h * h * (1.0 / 12.0);
   return c;
 }
+// Printed-form corrector (Eq. 4 with 3/20 and the predicted base): its velocity update
+// equals the time-symmetric one, its position update is
+//   x_{k+1} = XP + (3/20) h^2 a_k - (1/30) h^3 j_k,  XP = x_p - (3/20) h^2 a0 - (7/60) h^3 j0.
+struct PCoef {
+  double pa, pj, ca, cj;
+};
+__device__ __forceinline__ PCoef pcoef(double h) {
+  PCoef c;
+  const double h2 = h * h, h3 = h2 * h;
+  c.pa = -0.15 * h2;
+  c.pj = -(7.0 / 60.0) * h3;
+  c.ca = 0.15 * h2;
+  c.cj = -(1.0 / 30.0) * h3;
+  return c;
+}
 __device__ __forceinline__ HCoef hsel(bool p, const HCoef &a, const HCoef &b) {
   HCoef c;
   c.h = p ? a.h : b.h;
@@ -60,6 +75,46 @@ __device__ __forceinline__ void pair_geom(const double (&xi)[3], const double (&
   double cc = -3.0 * (rv * rho2);
 #pragma unroll
   for (int c = 0; c < 3; c++) w[c] = fma(cc, dx[c], dv[c]);
+}
+
+// ---------------------------------------------------------------- group collectives
+// All lanes of the warp execute these (full-mask shuffles); each group of N lanes
+// starting at `base` reduces its own values.
+template <int N>
+__device__ __forceinline__ double grp_sum(double val, int b, int base) {
+  // segmented tree: after the loop lane b = 0 of the group holds the sum
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, val, off);
+    val += (b + off < N) ? o : 0.0;
+  }
+  return shfl(val, base);
+}
+
+// exclusive prefix sum over the group (lane b gets the sum over lanes 0..b-1)
+template <int N>
+__device__ __forceinline__ double grp_scan_excl(double val, int b) {
+  double inc = val;
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_up_sync(0xffffffffu, inc, off);
+    inc += (b >= off) ? o : 0.0;
+  }
+  double ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  return b > 0 ? ex : 0.0;
+}
+
+// exclusive suffix sum (lane b gets the sum over lanes b+1..N-1)
+template <int N>
+__device__ __forceinline__ double grp_suffix_excl(double val, int b) {
+  double inc = val;
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, inc, off);
+    inc += (b + off < N) ? o : 0.0;
+  }
+  double ex = __shfl_down_sync(0xffffffffu, inc, 1);
+  return b + 1 < N ? ex : 0.0;
 }
 
 // ---------------------------------------------------------------- body per lane ("ring")

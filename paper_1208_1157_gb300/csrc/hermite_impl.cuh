@@ -10,6 +10,7 @@ namespace swarm {
 // One work unit = one warp's G = 32/N systems of a bin, integrated for the whole call.
 template <int N>
 __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepParams &P, int unit) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
   using R = Ring<N>;
   constexpr int G = R::G;
   constexpr int RT = R::RT > 0 ? R::RT : 1;
@@ -74,17 +75,29 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
     for (int c = 0; c < 3; c++) {
       xk[c] = fma(j0[c], C.h3_6, fma(a0[c], C.h2_2, fma(v[c], C.h, x[c])));
       vk[c] = fma(j0[c], C.h2_2, fma(a0[c], C.h, v[c]));
-      Xb[c] = fma(a0[c], C.h2_12, fma(v[c], C.hh, x[c]));
       Vb[c] = fma(j0[c], C.h2_12, fma(a0[c], C.hh, v[c]));
+    }
+    PCoef PC;
+    if (printed) {
+      PC = pcoef(C.h);
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(j0[c], PC.pj, fma(a0[c], PC.pa, xk[c]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(a0[c], C.h2_12, fma(v[c], C.hh, x[c]));
     }
     // corrector passes (time-symmetric form of Eq. 4)
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[3], jk[3];
       ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
-        xk[c] = fma(-C.h2_12, ak[c], fma(C.hh, vk[c], Xb[c]));
+      for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
+      if (printed) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(PC.cj, jk[c], fma(PC.ca, ak[c], Xb[c]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(-C.h2_12, ak[c], fma(C.hh, vk[c], Xb[c]));
       }
     }
     // third evaluation: next step's a0, j0 and the monitor's distances
@@ -161,6 +174,7 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
 // ---------------------------------------------------------------- system per lane
 template <int N>
 __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepParams &P, int unit) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
   const int s = unit * 32 + (threadIdx.x & 31);
   if (s >= B.S) return;
   const int SP = B.S_pad;
@@ -204,19 +218,39 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
       for (int c = 0; c < 3; c++) {
         xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
         vk[i][c] = fma(j0[i][c], C.h2_2, fma(a0[i][c], C.h, v[i][c]));
-        Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
         Vb[i][c] = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
       }
+    PCoef PC;
+    if (printed) {
+      PC = pcoef(C.h);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
+    }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
       spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-          vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
-          xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
-        }
+        for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
+      if (printed) {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
+      }
     }
     spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
@@ -264,6 +298,315 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
   }
 }
 
+
+// ---------------------------------------------------------------- adaptive step (Eq. 5)
+// The Hermite propagator with the step of Sec. 4.3.2: dt = tau (sum_i |j_i|^2/|a_i|^2)^(-1/2)
+// from the values at the start of the step, clamped so that the last step lands on the
+// system's end time.  P.dt carries tau (its sign gives the direction).  A launch takes at
+// most P.max_steps (or 2^24) steps per system; a system that has not reached its end time
+// then stays ACTIVE.
+constexpr int kAdaptiveStepCap = 1 << 24;
+
+__device__ __forceinline__ double adaptive_end(const BinView &B, const StepParams &P, int s) {
+  return B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
+}
+
+template <int N>
+__device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, const StepParams &P, int unit) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
+  using R = Ring<N>;
+  constexpr int G = R::G;
+  constexpr int RT = R::RT > 0 ? R::RT : 1;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int s0 = unit * G;
+  int s = s0 + g;
+  const bool sys_ok = lane_ok && s < B.S;
+  if (s >= B.S) s = s0;
+  const int SP = B.S_pad;
+  double x[3], v[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x[c] = B.x[(size_t)(c * N + b) * SP + s];
+    v[c] = B.v[(size_t)(c * N + b) * SP + s];
+  }
+  const double m = B.m[(size_t)b * SP + s];
+  const double t0 = B.t[s];
+  const int st0 = B.status[s];
+  const double m0 = shfl(m, base);
+  const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
+  const double te = adaptive_end(B, P, s);
+  const double tau = fabs(P.dt), dir = P.dt > 0 ? 1.0 : -1.0;
+  bool alive = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
+  if (!__any_sync(FULL, alive)) {
+    if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+  double kc[RT];
+#pragma unroll
+  for (int r = 1; r <= RT; r++) {
+    int p = b + r;
+    if (p >= N) p -= N;
+    double mp = shfl(m, base + p);
+    kc[r - 1] = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+  }
+  double a0[3], j0[3], q2, d2[RT];
+  ring_accjerk<N, false>(x, v, m, b, base, a0, j0, q2, d2);
+  const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
+  double t = t0;
+  int steps_done = 0, code = 0;
+  bool reached = false, ran = alive;
+  for (int k = 1; k <= cap; k++) {
+    if (!__any_sync(FULL, alive)) break;
+    // Eq. 5 over the system's bodies (group sum of this lane's |j|^2/|a|^2)
+    const double ratio = (j0[0] * j0[0] + j0[1] * j0[1] + j0[2] * j0[2]) / (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
+    const double ssum = grp_sum<N>(ratio, b, base);
+    double h = tau * rsqrt(ssum);
+    const double rem = (te - t) * dir;
+    const bool last = h >= rem;
+    const bool bad = !(h > 0.0) || nonfinite(h);
+    h = (last ? rem : h) * dir;
+    const HCoef C = hcoef(h);
+    double xk[3], vk[3], Xb[3], Vb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      xk[c] = fma(j0[c], C.h3_6, fma(a0[c], C.h2_2, fma(v[c], C.h, x[c])));
+      vk[c] = fma(j0[c], C.h2_2, fma(a0[c], C.h, v[c]));
+      Vb[c] = fma(j0[c], C.h2_12, fma(a0[c], C.hh, v[c]));
+    }
+    PCoef PC;
+    if (printed) {
+      PC = pcoef(C.h);
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(j0[c], PC.pj, fma(a0[c], PC.pa, xk[c]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(a0[c], C.h2_12, fma(v[c], C.hh, x[c]));
+    }
+    for (int ic = 0; ic < P.n_corr; ic++) {
+      double ak[3], jk[3];
+      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+#pragma unroll
+      for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
+      if (printed) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(PC.cj, jk[c], fma(PC.ca, ak[c], Xb[c]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(-C.h2_12, ak[c], fma(C.hh, vk[c], Xb[c]));
+      }
+    }
+    double an[3], jn[3];
+    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    const bool active = alive && !bad;
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[c] = xk[c];
+        v[c] = vk[c];
+        a0[c] = an[c];
+        j0[c] = jn[c];
+      }
+      steps_done = k;
+      t = last ? te : t + h;
+    }
+    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
+                    nonfinite(v[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+#pragma unroll
+    for (int r = 1; r <= RT; r++) {
+      int p = b + r;
+      if (p >= N) p -= N;
+      double q2p = shfl(q2, base + p);
+      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+    }
+    const unsigned gm = ((1u << N) - 1u) << base;
+    const unsigned bnf = __ballot_sync(FULL, alive && (nf || bad)) & gm;
+    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+    const int c2 = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (alive && c2) {
+      code = c2;
+      alive = false;
+    } else if (active && last) {
+      reached = true;
+      alive = false;
+    }
+    if (P.log_interval > 0 && (k % P.log_interval) == 0) {
+      double e[4];
+      ring_energy<N>(x, v, m, b, base, e);
+      if (active && !c2 && b == 0 && sys_ok) write_log(P, B.gidx[s], t, e);
+    }
+  }
+  if (sys_ok && ran) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      B.x[(size_t)(c * N + b) * SP + s] = x[c];
+      B.v[(size_t)(c * N + b) * SP + s] = v[c];
+    }
+    if (b == 0) {
+      B.t[s] = t;
+      B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+    }
+  } else if (runnable && b == 0) {
+    B.status[s] = SWARM_SYS_DONE;  // already at its end time
+  }
+  if (P.counters && sys_ok && b == 0 && steps_done > 0) {
+    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+    atomicAdd(&P.counters[0], (unsigned long long)steps_done);
+    atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done * (P.n_corr + 1)));
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, const StepParams &P, int unit) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
+  const int s = unit * 32 + (threadIdx.x & 31);
+  if (s >= B.S) return;
+  const int SP = B.S_pad;
+  double x[N][3], v[N][3], m[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    m[i] = B.m[(size_t)i * SP + s];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      x[i][c] = B.x[(size_t)(c * N + i) * SP + s];
+      v[i][c] = B.v[(size_t)(c * N + i) * SP + s];
+    }
+  }
+  const double t0 = B.t[s];
+  if (B.status[s] > SWARM_SYS_DONE) return;
+  const double te = adaptive_end(B, P, s);
+  const double tau = fabs(P.dt), dir = P.dt > 0 ? 1.0 : -1.0;
+  if (!((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)))) {
+    B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+  double kc[N][N];
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
+  double a0[N][3], j0[N][3], q2[N], d2[N][N];
+  spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+  const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
+  double t = t0;
+  int steps_done = 0, code = 0;
+  bool reached = false;
+  for (int k = 1; k <= cap; k++) {
+    double ssum = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      ssum += (j0[i][0] * j0[i][0] + j0[i][1] * j0[i][1] + j0[i][2] * j0[i][2]) /
+              (a0[i][0] * a0[i][0] + a0[i][1] * a0[i][1] + a0[i][2] * a0[i][2]);
+    double h = tau * rsqrt(ssum);
+    if (!(h > 0.0) || nonfinite(h)) {
+      code = SWARM_SYS_NONFINITE;
+      break;
+    }
+    const double rem = (te - t) * dir;
+    const bool last = h >= rem;
+    h = (last ? rem : h) * dir;
+    const HCoef C = hcoef(h);
+    double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
+        vk[i][c] = fma(j0[i][c], C.h2_2, fma(a0[i][c], C.h, v[i][c]));
+        Vb[i][c] = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
+      }
+    PCoef PC;
+    if (printed) {
+      PC = pcoef(C.h);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
+    }
+    for (int ic = 0; ic < P.n_corr; ic++) {
+      double ak[N][3], jk[N][3];
+      spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
+      if (printed) {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
+      }
+    }
+    spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[i][c] = xk[i][c];
+        v[i][c] = vk[i][c];
+      }
+    steps_done = k;
+    t = last ? te : t + h;
+    bool nf = false, ej = false, ce = false;
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
+#pragma unroll
+    for (int i = 1; i < N; i++) ej |= (P.eject2 > 0.0) && (q2[i] > P.eject2);
+#pragma unroll
+    for (int i = 1; i < N; i++)
+#pragma unroll
+      for (int k2 = i + 1; k2 < N; k2++)
+        if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+    code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (code) break;
+    if (P.log_interval > 0 && (k % P.log_interval) == 0) {
+      double e[4];
+      spl_energy<N>(x, v, m, e);
+      write_log(P, B.gidx[s], t, e);
+    }
+    if (last) {
+      reached = true;
+      break;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
+      B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
+    }
+  B.t[s] = t;
+  B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+  if (P.counters && steps_done > 0) {
+    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+    atomicAdd(&P.counters[0], (unsigned long long)steps_done);
+    atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps_done * (P.n_corr + 1)));
+  }
+}
+
 // Out-of-line copies called by the multi-body-count dispatcher kernel.
 template <int N>
 __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
@@ -273,11 +616,19 @@ template <int N>
 __device__ __noinline__ void spl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
   spl_hermite_body<N>(B, P, unit);
 }
+template <int N>
+__device__ __noinline__ void bpl_hermite_adaptive_unit(const BinView &B, const StepParams &P, int unit) {
+  bpl_hermite_adaptive_body<N>(B, P, unit);
+}
+template <int N>
+__device__ __noinline__ void spl_hermite_adaptive_unit(const BinView &B, const StepParams &P, int unit) {
+  spl_hermite_adaptive_body<N>(B, P, unit);
+}
 
 // Persistent kernel for one bin (one body count, one mapping): the unit body is inlined,
 // so registers are allocated for this n alone.  Warps pull unit indices from a counter.
 // MINB = 3 is the high-occupancy variant (registers capped for 3 CTAs of 128 threads per SM).
-template <int MAP, int N, int MINB>
+template <int MAP, int N, int MINB, bool ADAPT = false>
 __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, int nunits, StepParams P) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -285,21 +636,37 @@ __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, i
     if (lane == 0) w = atomicAdd(P.work_next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= nunits) break;
-    if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_body<N>(B, P, w);
-    else bpl_hermite_body<N>(B, P, w);
+    if (ADAPT) {
+      if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_adaptive_body<N>(B, P, w);
+      else bpl_hermite_adaptive_body<N>(B, P, w);
+    } else {
+      if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_body<N>(B, P, w);
+      else bpl_hermite_body<N>(B, P, w);
+    }
   }
 }
 
-template <int MAP, int N, int MINB = 2>
+template <int MAP, int N, int MINB = 2, bool ADAPT = false>
 cudaError_t launch_hermite_uniform_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st) {
-  hermite_uniform_kernel<MAP, N, MINB><<<grid, 128, 0, st>>>(B, nunits, P);
+  hermite_uniform_kernel<MAP, N, MINB, ADAPT><<<grid, 128, 0, st>>>(B, nunits, P);
   return cudaGetLastError();
 }
-template <int MAP, int N, int MINB = 2>
+template <int MAP, int N, int MINB = 2, bool ADAPT = false>
 int hermite_uniform_blocks_n() {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_uniform_kernel<MAP, N, MINB>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_uniform_kernel<MAP, N, MINB, ADAPT>, 128, 0);
   return nb;
+}
+// adaptive (Eq. 5) single-bin kernels: both mappings, registers sized for 2 CTAs per SM
+template <int MAP, int N>
+cudaError_t launch_hermite_uniform_pick(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
+                                        int *blocks, bool adaptive) {
+  if (adaptive) {
+    if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N, 2, true>();
+    return grid > 0 ? launch_hermite_uniform_n<MAP, N, 2, true>(B, nunits, P, grid, st) : cudaSuccess;
+  }
+  if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N>();
+  return grid > 0 ? launch_hermite_uniform_n<MAP, N>(B, nunits, P, grid, st) : cudaSuccess;
 }
 
 }  // namespace swarm

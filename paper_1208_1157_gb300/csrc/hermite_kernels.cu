@@ -10,6 +10,10 @@ template <int N>
 __device__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit);
 template <int N>
 __device__ void spl_hermite_unit(const BinView &B, const StepParams &P, int unit);
+template <int N>
+__device__ void bpl_hermite_adaptive_unit(const BinView &B, const StepParams &P, int unit);
+template <int N>
+__device__ void spl_hermite_adaptive_unit(const BinView &B, const StepParams &P, int unit);
 
 // ---------------------------------------------------------------- persistent launch
 // Warps pull (bin, unit, mapping) items from a cost-ordered list until it is empty.
@@ -24,32 +28,43 @@ __global__ void __launch_bounds__(128, 2)
     if (w >= nwork) break;
     const int4 it = work[w];
     const BinView B = bins[it.x];
+    const bool ad = P.integrator == SWARM_HERMITE4_ADAPTIVE;
+#define SPL_CASE(NN) \
+  case NN:           \
+    if (ad) spl_hermite_adaptive_unit<NN>(B, P, it.y); else spl_hermite_unit<NN>(B, P, it.y); \
+    break;
+#define BPL_CASE(NN) \
+  case NN:           \
+    if (ad) bpl_hermite_adaptive_unit<NN>(B, P, it.y); else bpl_hermite_unit<NN>(B, P, it.y); \
+    break;
     if (it.z == SWARM_MAP_SYSTEM_PER_LANE) {
       switch (B.n) {
-        case 2: spl_hermite_unit<2>(B, P, it.y); break;
-        case 3: spl_hermite_unit<3>(B, P, it.y); break;
-        case 4: spl_hermite_unit<4>(B, P, it.y); break;
+        SPL_CASE(2)
+        SPL_CASE(3)
+        SPL_CASE(4)
         default: break;
       }
     } else {
       switch (B.n) {
-        case 2: bpl_hermite_unit<2>(B, P, it.y); break;
-        case 3: bpl_hermite_unit<3>(B, P, it.y); break;
-        case 4: bpl_hermite_unit<4>(B, P, it.y); break;
-        case 5: bpl_hermite_unit<5>(B, P, it.y); break;
-        case 6: bpl_hermite_unit<6>(B, P, it.y); break;
-        case 7: bpl_hermite_unit<7>(B, P, it.y); break;
-        case 8: bpl_hermite_unit<8>(B, P, it.y); break;
-        case 9: bpl_hermite_unit<9>(B, P, it.y); break;
-        case 10: bpl_hermite_unit<10>(B, P, it.y); break;
-        case 11: bpl_hermite_unit<11>(B, P, it.y); break;
-        case 12: bpl_hermite_unit<12>(B, P, it.y); break;
-        case 13: bpl_hermite_unit<13>(B, P, it.y); break;
-        case 14: bpl_hermite_unit<14>(B, P, it.y); break;
-        case 15: bpl_hermite_unit<15>(B, P, it.y); break;
+        BPL_CASE(2)
+        BPL_CASE(3)
+        BPL_CASE(4)
+        BPL_CASE(5)
+        BPL_CASE(6)
+        BPL_CASE(7)
+        BPL_CASE(8)
+        BPL_CASE(9)
+        BPL_CASE(10)
+        BPL_CASE(11)
+        BPL_CASE(12)
+        BPL_CASE(13)
+        BPL_CASE(14)
+        BPL_CASE(15)
         default: break;
       }
     }
+#undef SPL_CASE
+#undef BPL_CASE
   }
 }
 

@@ -1,31 +1,25 @@
-// Single-bin persistent Hermite kernels (body per lane), n = 2..8.
+// Single-bin persistent Hermite kernels (body per lane), n = 2..8; fixed and adaptive (Eq. 5) steps.
 #include "hermite_impl.cuh"
 
 namespace swarm {
 
 cudaError_t launch_hermite_uniform_bpl_a(int n, const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st, int *blocks) {
+  const bool ad = P.integrator == SWARM_HERMITE4_ADAPTIVE;
   switch (n) {
     case 2:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 2>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 2>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 2>(B, nunits, P, grid, st, blocks, ad);
     case 3:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 3>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 3>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 3>(B, nunits, P, grid, st, blocks, ad);
     case 4:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 4>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 4>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 4>(B, nunits, P, grid, st, blocks, ad);
     case 5:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 5>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 5>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 5>(B, nunits, P, grid, st, blocks, ad);
     case 6:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 6>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 6>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 6>(B, nunits, P, grid, st, blocks, ad);
     case 7:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 7>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 7>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 7>(B, nunits, P, grid, st, blocks, ad);
     case 8:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 8>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 8>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 8>(B, nunits, P, grid, st, blocks, ad);
     default:
       return cudaErrorInvalidValue;
   }

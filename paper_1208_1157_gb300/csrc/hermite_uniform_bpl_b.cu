@@ -1,31 +1,25 @@
-// Single-bin persistent Hermite kernels (body per lane), n = 9..15.
+// Single-bin persistent Hermite kernels (body per lane), n = 9..15; fixed and adaptive (Eq. 5) steps.
 #include "hermite_impl.cuh"
 
 namespace swarm {
 
 cudaError_t launch_hermite_uniform_bpl_b(int n, const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st, int *blocks) {
+  const bool ad = P.integrator == SWARM_HERMITE4_ADAPTIVE;
   switch (n) {
     case 9:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 9>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 9>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 9>(B, nunits, P, grid, st, blocks, ad);
     case 10:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 10>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 10>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 10>(B, nunits, P, grid, st, blocks, ad);
     case 11:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 11>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 11>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 11>(B, nunits, P, grid, st, blocks, ad);
     case 12:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 12>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 12>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 12>(B, nunits, P, grid, st, blocks, ad);
     case 13:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 13>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 13>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 13>(B, nunits, P, grid, st, blocks, ad);
     case 14:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 14>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 14>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 14>(B, nunits, P, grid, st, blocks, ad);
     case 15:
-      if (blocks) *blocks = hermite_uniform_blocks_n<SWARM_MAP_BODY_PER_LANE, 15>();
-      return grid > 0 ? launch_hermite_uniform_n<SWARM_MAP_BODY_PER_LANE, 15>(B, nunits, P, grid, st) : cudaSuccess;
+      return launch_hermite_uniform_pick<SWARM_MAP_BODY_PER_LANE, 15>(B, nunits, P, grid, st, blocks, ad);
     default:
       return cudaErrorInvalidValue;
   }

@@ -12,46 +12,6 @@
 
 namespace swarm {
 
-// ---------------------------------------------------------------- group collectives
-// All lanes of the warp execute these (full-mask shuffles); each group of N lanes
-// starting at `base` reduces its own values.
-template <int N>
-__device__ __forceinline__ double grp_sum(double val, int b, int base) {
-  // segmented tree: after the loop lane b = 0 of the group holds the sum
-#pragma unroll
-  for (int off = 1; off < N; off <<= 1) {
-    double o = __shfl_down_sync(0xffffffffu, val, off);
-    val += (b + off < N) ? o : 0.0;
-  }
-  return shfl(val, base);
-}
-
-// exclusive prefix sum over the group (lane b gets the sum over lanes 0..b-1)
-template <int N>
-__device__ __forceinline__ double grp_scan_excl(double val, int b) {
-  double inc = val;
-#pragma unroll
-  for (int off = 1; off < N; off <<= 1) {
-    double o = __shfl_up_sync(0xffffffffu, inc, off);
-    inc += (b >= off) ? o : 0.0;
-  }
-  double ex = __shfl_up_sync(0xffffffffu, inc, 1);
-  return b > 0 ? ex : 0.0;
-}
-
-// exclusive suffix sum (lane b gets the sum over lanes b+1..N-1)
-template <int N>
-__device__ __forceinline__ double grp_suffix_excl(double val, int b) {
-  double inc = val;
-#pragma unroll
-  for (int off = 1; off < N; off <<= 1) {
-    double o = __shfl_down_sync(0xffffffffu, inc, off);
-    inc += (b + off < N) ? o : 0.0;
-  }
-  double ex = __shfl_down_sync(0xffffffffu, inc, 1);
-  return b + 1 < N ? ex : 0.0;
-}
-
 // ---------------------------------------------------------------- acceleration ring
 // Acceleration only (Eq. 1), over M members at lanes base+OFF .. base+OFF+M-1; member j.
 // Lanes outside the members (the centre-of-mass lane in DH) mirror member 0 and their

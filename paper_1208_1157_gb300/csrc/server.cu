@@ -473,11 +473,46 @@ extern "C" int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, d
   return SWARM_OK;
 }
 
+// Cancel a queued or running request: a queued one leaves the queue, a running one gives
+// its slots back (their systems are marked free on the device).  Its state becomes
+// SWARM_REQ_CANCELLED; release it like a finished one.
+extern "C" int swarm_server_cancel(swarm_server *sv, int64_t id) {
+  if (!sv) return sfail(SWARM_EINVAL, "NULL server");
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(SWARM_EINVAL, "unknown request id");
+  Request *r = it->second.get();
+  if (r->state == SWARM_REQ_DONE || r->state == SWARM_REQ_CANCELLED) return sfail(SWARM_ESTATE, "request already finished");
+  if (r->state == SWARM_REQ_QUEUED) {
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+      if (*q == id) {
+        sv->queue.erase(q);
+        break;
+      }
+  } else {
+    Pool *p = r->pool;
+    std::vector<int32_t> freeval(r->slots.size(), kFree);
+    for (size_t i = 0; i < r->slots.size(); i++)
+      SCK(cudaMemcpyAsync(p->view.status + r->slots[i], &freeval[i], sizeof(int32_t), cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaStreamSynchronize(sv->stream));
+    for (int sl : r->slots) {
+      p->owner[sl] = -1;
+      p->free_slots.insert(sl);
+      p->unit_occ[sl / p->per]--;
+    }
+    r->slots.clear();
+  }
+  r->state = SWARM_REQ_CANCELLED;
+  r->finished = Clock::now();
+  sv->stats.cancelled++;
+  return SWARM_OK;
+}
+
 extern "C" int swarm_server_release(swarm_server *sv, int64_t id) {
   if (!sv) return sfail(SWARM_EINVAL, "NULL server");
   auto it = sv->reqs.find(id);
   if (it == sv->reqs.end()) return sfail(SWARM_EINVAL, "unknown request id");
-  if (it->second->state != SWARM_REQ_DONE) return sfail(SWARM_ESTATE, "request is not finished");
+  if (it->second->state != SWARM_REQ_DONE && it->second->state != SWARM_REQ_CANCELLED)
+    return sfail(SWARM_ESTATE, "request is not finished");
   sv->reqs.erase(it);
   return SWARM_OK;
 }

@@ -11,7 +11,7 @@ import numpy as np
 from . import ics
 from . import swarm as S
 
-REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED = 0, 1, 2, 3
 
 
 class Config(C.Structure):
@@ -23,7 +23,7 @@ class Config(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("submitted", "admitted", "completed", "queued", "occupied_slots",
                                          "pool_slots", "device_bytes", "quanta", "system_steps", "pair_evaluations")] + \
-               [("kernel_ms", C.c_double)]
+               [("kernel_ms", C.c_double), ("cancelled", C.c_int64)]
 
 
 _decl = False
@@ -40,6 +40,7 @@ def _lib():
         L.swarm_server_step.argtypes = [vp, ip]
         L.swarm_server_poll.argtypes = [vp, C.c_int64, ip, dp, dp, dp, ip, dp]
         L.swarm_server_release.argtypes = [vp, C.c_int64]
+        L.swarm_server_cancel.argtypes = [vp, C.c_int64]
         L.swarm_server_query.argtypes = [vp, C.POINTER(Stats)]
         L.swarm_server_destroy.argtypes = [vp]
         L.swarm_server_destroy.restype = None
@@ -104,6 +105,9 @@ class Server:
             return st.value, None
         S._check(_lib().swarm_server_poll(self._h, rid, C.byref(st), None, None, None, None, None))
         return st.value, None
+
+    def cancel(self, rid: int):
+        S._check(_lib().swarm_server_cancel(self._h, rid))
 
     def release(self, rid: int):
         S._check(_lib().swarm_server_release(self._h, rid))

@@ -16,10 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswarm_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
-HERMITE4, MVS_DH, MVS_JACOBI = 1, 2, 3
+HERMITE4, MVS_DH, MVS_JACOBI, HERMITE4_ADAPTIVE = 1, 2, 3, 4
 ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE = range(6)
 MAP_AUTO, MAP_SYSTEM_PER_LANE, MAP_BODY_PER_LANE, MAP_PLAIN_PER_STEP = range(4)
-OPT_MAPPING, OPT_N_CORR, OPT_LOG_INTERVAL, OPT_LOG_CAPACITY, OPT_STEPS_PER_LAUNCH, OPT_SINGLE_LAUNCH, OPT_CTAS_PER_SM = range(1, 8)
+OPT_MAPPING, OPT_N_CORR, OPT_LOG_INTERVAL, OPT_LOG_CAPACITY, OPT_STEPS_PER_LAUNCH, OPT_SINGLE_LAUNCH, OPT_CTAS_PER_SM, OPT_CORRECTOR = range(1, 9)
 
 # every symbol include/swarm.h declares (checked by the ABI test)
 EXPORTS = (
@@ -206,6 +206,15 @@ def tuner_choice(n, integrator, n_sys, stream=None):
     m, c = C.c_int32(), C.c_int32()
     _check(lib().swarm_tuner_choice(int(n), int(integrator), int(n_sys), _stream_ptr(stream), C.byref(m), C.byref(c)))
     return m.value, c.value
+
+
+def tuner_load(path: str) -> None:
+    """Load saved tuner choices (a missing file is not an error)."""
+    _check(lib().swarm_tuner_load(path.encode()))
+
+
+def tuner_save(path: str) -> None:
+    _check(lib().swarm_tuner_save(path.encode()))
 
 
 def version() -> str:

@@ -173,3 +173,48 @@ def test_chunked_launches_replayed_from_a_cuda_graph(mapping):
     assert ex.max() <= 1e-14 and ev.max() <= 1e-14
     np.testing.assert_allclose(got["time"], ref["time"], rtol=1e-14)
     assert np.all(got["status"] == O.DONE)
+
+
+@pytest.mark.parametrize("mapping", [1, 2])
+def test_adaptive_step_hermite_parity(mapping):
+    # Eq. 5 steps with tau = 0.01 over two inner orbits, stops on
+    ens = ics.three_body(200, seed=16)
+    t_end = 2 * TWO_PI
+    o = run_oracle(ens, t_end, O.HERMITE_ADAPTIVE, 0.01, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, t_end, O.HERMITE_ADAPTIVE, 0.01, ce=3.0, ej=100.0)
+    g = run_gpu(ens, t_end, 4, 0.01, mapping=mapping, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens, steps=2000)
+    assert np.all(g["time"][g["status"] == O.DONE] == t_end)
+
+
+def test_adaptive_step_hermite_ragged_and_backwards():
+    ens = ics.ragged(150, seed=17)
+    t_end = 1.5 * TWO_PI
+    o = run_oracle(ens, t_end, O.HERMITE_ADAPTIVE, 0.02, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, t_end, O.HERMITE_ADAPTIVE, 0.02, ce=3.0, ej=100.0)
+    g = run_gpu(ens, t_end, 4, 0.02, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens, steps=3000)
+    # a negative tau integrates back to the start time
+    from paper_1208_1157_gb300 import swarm as S
+    with S.Ensemble(ens) as e:
+        e.integrate(t_end, S.HERMITE4_ADAPTIVE, 0.005)
+        e.integrate(0.0, S.HERMITE4_ADAPTIVE, -0.005)
+        back = e.state()
+    assert np.all(back["time"] == 0.0)
+    ex, ev = per_system_errors(ens, back, ens)
+    assert np.median(np.maximum(ex, ev)) < 1e-8
+
+
+@pytest.mark.parametrize("mapping", [1, 2])
+def test_printed_form_corrector_parity(mapping):
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.three_body(128, seed=18)
+    o = O.integrate(ens, 1000 * DT, DT, O.HERMITE, corr_form=O.CORR_PRINTED, ce_factor=3.0, eject_radius=100.0)
+    with S.Ensemble(ens) as e:
+        e.set_option(S.OPT_MAPPING, mapping)
+        e.set_option(S.OPT_CORRECTOR, 1)
+        e.set_stop(3.0, 100.0)
+        e.integrate(1000 * DT, S.HERMITE4, DT)
+        g = e.state()
+    assert_parity(ens, g, o)

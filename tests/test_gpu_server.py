@@ -111,3 +111,39 @@ def test_stopped_systems_retire_with_their_request():
     res = out["done"][0]
     assert res["status"][6] == 3 and np.all(np.delete(res["status"], 6) == 1)
     check_same([q], [e], out)
+
+
+def test_cancel_and_impossible_admission():
+    # fault injection on the host: a request too large for any pool is refused, a queued
+    # request and a running one are cancelled; the others still finish with the same results
+    from paper_1208_1157_gb300 import server as SV
+    from paper_1208_1157_gb300 import swarm as S
+
+    trace = [{"id": r, "arrival_s": 0.0, "n_sys": 40, "n": 4, "integrator": 1, "t_end": (60 + 20 * r) * HDT,
+              "seed": 5000 + r} for r in range(4)]
+    ens_list = [ics.request_ensemble(q) for q in trace]
+    with SV.Server(slots_per_pool=96, quantum_steps=20) as sv:
+        big = ics.request_ensemble({"n_sys": 97, "n": 4, "seed": 9})
+        with pytest.raises(S.SwarmError):
+            sv.submit(big, 1.0, 1)  # larger than a pool: never admissible
+        ids = [sv.submit(e, q["t_end"], 1) for e, q in zip(ens_list, trace)]
+        sv.step()  # requests 0 and 1 fit (80 of 96 slots); 2 and 3 wait
+        assert sv.poll(ids[0])[0] == SV.REQ_RUNNING and sv.poll(ids[3])[0] == SV.REQ_QUEUED
+        sv.cancel(ids[1])   # running: its 40 slots are freed
+        sv.cancel(ids[3])   # queued: leaves the queue
+        with pytest.raises(S.SwarmError):
+            sv.cancel(ids[3])
+        for _ in range(100):
+            sv.step()
+            if sv.stats()["completed"] == 2:
+                break
+        st = sv.stats()
+        assert st["completed"] == 2 and st["cancelled"] == 2 and st["queued"] == 0
+        out = {"done": {}}
+        for r in (0, 2):
+            state, res = sv.poll(ids[r], trace[r]["n_sys"], trace[r]["n"])
+            assert state == SV.REQ_DONE
+            out["done"][r] = res
+        assert sv.poll(ids[1])[0] == SV.REQ_CANCELLED
+        sv.release(ids[1])
+    check_same([trace[0], trace[2]], [ens_list[0], ens_list[2]], {"done": {0: out["done"][0], 1: out["done"][2]}})

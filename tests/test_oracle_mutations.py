@@ -32,6 +32,7 @@ MUTANTS = {
     "dh_drift_mass": ("q[3 * i + c] += h * p[c] / m[0];", "q[3 * i + c] += h * p[c];"),
     "jacobi_mu": ("double mu = m[0] * eta_i / eta;", "double mu = m[0];"),
     "jacobi_transform": ("R[c] -= m[i] / eta[i] * r[3 * i + c];", "R[c] -= m[i] / eta[i - 1] * r[3 * i + c];"),
+    "adaptive_dt_square": ("s += dot3(j, j) / dot3(a, a);", "s += sqrt(dot3(j, j) / dot3(a, a));"),
     "monitor_hill_cube": ("cbrt((m[i] + m[j]) / (3.0 * m[0]))", "sqrt((m[i] + m[j]) / (3.0 * m[0]))"),
 }
 

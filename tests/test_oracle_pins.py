@@ -195,6 +195,38 @@ def test_hermite_conservation_and_energy_order():
     assert dE[0] / dE[1] > 8.0, dE
 
 
+# ----------------------------------------------------------------- Eq. 5 adaptive step
+def test_adaptive_step_of_a_circular_two_body_orbit():
+    # circular motion: a = -w^2 r, j = -w^2 v for both bodies, so |j|/|a| = w and
+    # Eq. 5 gives tau / (sqrt(2) w) with w = sqrt(mu / a^3)
+    m0, m1, a = 1.0, 1e-3, 1.7
+    s = ics.two_body(a, 0.0, m0, m1)
+    a0, j0 = O.accjerk(s["mass"], s["pos"], s["vel"])
+    w = math.sqrt((m0 + m1) / a ** 3)
+    assert O.adaptive_dt(a0, j0, 0.02) == pytest.approx(0.02 / (math.sqrt(2) * w), rel=1e-13)
+
+
+def test_adaptive_hermite_lands_on_t_end_and_is_fourth_order_in_tau():
+    m0, m1 = 1.0, 1e-3
+    mu = m0 + m1
+    T = cf.period(mu, 1.0)
+    errs = []
+    for tau in (0.02, 0.01, 0.005):
+        s = ics.two_body(1.0, 0.5, m0, m1)
+        out = O.integrate(s, T, tau, O.HERMITE_ADAPTIVE)
+        assert out["time"][0] == T and out["status"][0] == O.DONE
+        r_ref, _ = cf.elliptic_at(mu, 1.0, 0.5, 0.0, T)
+        errs.append(np.linalg.norm(out["pos"][1] - out["pos"][0] - r_ref))
+    for a, b in zip(errs, errs[1:]):
+        assert 12.0 <= a / b <= 20.0, errs
+    # backwards with a negative tau returns close to the start
+    s = ics.two_body(1.0, 0.5, m0, m1)
+    fwd = O.integrate(s, T / 3, 0.005, O.HERMITE_ADAPTIVE)
+    back = O.integrate({**s, "pos": fwd["pos"], "vel": fwd["vel"]}, 0.0, -0.005, O.HERMITE_ADAPTIVE, time=fwd["time"])
+    assert back["time"][0] == 0.0
+    assert rel(back["pos"], s["pos"]) < 1e-9
+
+
 # ----------------------------------------------------------------- Eq. 6, L
 def test_energy_and_angular_momentum_hand_values():
     m = np.array([1.0, 0.5])
