@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE = range(6)
-HERMITE, MVS_DH, MVS_JACOBI, HERMITE_ADAPTIVE = 1, 2, 3, 4
+HERMITE, MVS_DH, MVS_JACOBI, HERMITE_ADAPTIVE, RKCK, RKCK_ADAPTIVE = 1, 2, 3, 4, 5, 6
 CORR_KOKUBO, CORR_PRINTED = 0, 1
 
 _lock = threading.Lock()
@@ -77,8 +77,11 @@ def _declare(L):
     L.or_jacobi_interaction_acc.argtypes = [C.c_int, _dp, _dp, _dp]
     L.or_integrate_ensemble.argtypes = [C.c_int, _ip, _dp, _dp, _dp, _dp, _ip, C.c_double, C.c_double, C.c_int,
                                         C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _dp, _ip,
-                                        C.POINTER(C.c_longlong)]
+                                        C.POINTER(C.c_longlong), C.c_double]
     L.or_integrate_ensemble.restype = C.c_int
+    L.or_rkck_tableau.argtypes = [_dp, _dp, _dp, _dp]
+    L.or_rkck_step.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, _dp]
+    L.or_rkck_step.restype = C.c_double
 
 
 def _d(a):
@@ -187,10 +190,24 @@ def mvs_step(kind, m, q, u, acc_cache, dt):
     return q, u, a, int(st)
 
 
+def rkck_tableau():
+    c, a, b5, b4 = np.zeros(6), np.zeros(36), np.zeros(6), np.zeros(6)
+    lib().or_rkck_tableau(_d(c), _d(a), _d(b5), _d(b4))
+    return c, a.reshape(6, 6), b5, b4
+
+
+def rkck_step(m, x, v, h):
+    """One Cash-Karp step; returns (x, v, scaled error, error vector [2n][3])."""
+    m, x, v = _f64(m), _f64(x, (-1, 3)), _f64(v, (-1, 3))
+    err = np.zeros((2 * len(m), 3))
+    e = lib().or_rkck_step(len(m), _d(m), _d(x), _d(v), float(h), _d(err))
+    return x, v, float(e), err
+
+
 # ---------------------------------------------------------------- ensembles
 def integrate(ens: dict, t_end: float, dt: float, integrator: int = HERMITE, n_corr: int = 2,
               corr_form: int = CORR_KOKUBO, ce_factor: float = 0.0, eject_radius: float = 0.0,
-              log_interval: int = 0, log_cap: int = 0, time=None, status=None) -> dict:
+              log_interval: int = 0, log_cap: int = 0, time=None, status=None, rk_eps: float = 1e-12) -> dict:
     """Integrate every system of `ens` (the ics layout) from `time` (default 0) to t_end."""
     n_body = np.ascontiguousarray(ens["n_body"], dtype=np.int32)
     S = len(n_body)
@@ -207,7 +224,7 @@ def integrate(ens: dict, t_end: float, dt: float, integrator: int = HERMITE, n_c
                                      stt.ctypes.data_as(_ip), float(t_end), float(dt), int(integrator),
                                      int(n_corr), int(corr_form), float(ce_factor), float(eject_radius),
                                      int(log_interval), max(cap, 1), _d(log), cnt.ctypes.data_as(_ip),
-                                     C.byref(kit))
+                                     C.byref(kit), float(rk_eps))
     if rc != 0:
         raise ValueError(f"oracle integrate rejected its arguments (rc={rc})")
     return {"pos": pos, "vel": vel, "time": tm, "status": stt, "log": log[:, :cap], "log_count": cnt,

@@ -16,6 +16,10 @@
  *    Jacobi-coordinate kick-Kepler-kick map of Wisdom & Holman 1991.
  *  - Kepler drift in universal variables (Danby 1988; Curtis, "Orbital Mechanics
  *    for Engineering Students", Sec. 3.7), Newton, tolerance 1e-14, at most 50 iterations.
+ *  - Runge-Kutta Cash-Karp (Sec. 2.2.2): the 5th-order solution is propagated (local
+ *    extrapolation); the adaptive version's error norm is relative to the system's largest
+ *    body position and velocity, and its step control is the standard controller of
+ *    Hairer, Norsett & Wanner (Sec. II.4) with safety 0.9 and step ratios in [0.2, 5].
  */
 #include "oracle.h"
 
@@ -431,12 +435,88 @@ int or_mvs_jacobi_step(int n, const double *m, double *r, double *w, double *acc
   return st;
 }
 
+/* ---------------- Runge-Kutta Cash-Karp 4(5) (Sec. 2.2.2, Sec. 4.3.3) ---------------- */
+/* The embedded pair of Cash & Karp, ACM TOMS 16 (1990) 201: nodes, stage coefficients,
+ * 5th-order weights (propagated solution) and embedded 4th-order weights. */
+static const double RK_C[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+static const double RK_A[6][6] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 5.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0.0, 0.0, 0.0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0.0, 0.0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0, 0.0}};
+static const double RK_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+static const double RK_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0,
+                                1.0 / 4.0};
+
+void or_rkck_tableau(double *c, double *a, double *b5, double *b4) {
+  for (int i = 0; i < 6; i++) {
+    c[i] = RK_C[i];
+    b5[i] = RK_B5[i];
+    b4[i] = RK_B4[i];
+    for (int j = 0; j < 6; j++) a[6 * i + j] = RK_A[i][j];
+  }
+}
+
+/* One step of y' = f(y), y = (x, v), f(y) = (v, a(x)): stage s is evaluated at
+ * y + h sum_{j<s} A[s][j] k_j; the step returns y + h sum_s B5[s] k_s and the error
+ * h sum_s (B5[s] - B4[s]) k_s. */
+double or_rkck_step(int n, const double *m, double *x, double *v, double h, double *err) {
+  double kx[6][3 * MAXN], kv[6][3 * MAXN], xs[3 * MAXN], vs[3 * MAXN];
+  int d = 3 * n;
+  for (int s = 0; s < 6; s++) {
+    for (int q = 0; q < d; q++) {
+      double sx = 0.0, sv = 0.0;
+      for (int j = 0; j < s; j++) {
+        sx += RK_A[s][j] * kx[j][q];
+        sv += RK_A[s][j] * kv[j][q];
+      }
+      xs[q] = x[q] + h * sx;
+      vs[q] = v[q] + h * sv;
+    }
+    for (int q = 0; q < d; q++) kx[s][q] = vs[q];
+    or_acc(n, m, xs, kv[s]);
+  }
+  double X = 0.0, V = 0.0;
+  for (int b = 0; b < n; b++) {
+    X = fmax(X, sqrt(dot3(x + 3 * b, x + 3 * b)));
+    V = fmax(V, sqrt(dot3(v + 3 * b, v + 3 * b)));
+  }
+  double ex[3 * MAXN], ev[3 * MAXN];
+  for (int q = 0; q < d; q++) {
+    double sx = 0.0, sv = 0.0, tx = 0.0, tv = 0.0;
+    for (int s = 0; s < 6; s++) {
+      sx += RK_B5[s] * kx[s][q];
+      sv += RK_B5[s] * kv[s][q];
+      tx += (RK_B5[s] - RK_B4[s]) * kx[s][q];
+      tv += (RK_B5[s] - RK_B4[s]) * kv[s][q];
+    }
+    ex[q] = h * tx;
+    ev[q] = h * tv;
+    x[q] += h * sx;
+    v[q] += h * sv;
+  }
+  double e = 0.0;
+  for (int b = 0; b < n; b++) {
+    e = fmax(e, sqrt(dot3(ex + 3 * b, ex + 3 * b)) / X);
+    e = fmax(e, sqrt(dot3(ev + 3 * b, ev + 3 * b)) / V);
+  }
+  if (err)
+    for (int q = 0; q < d; q++) {
+      err[q] = ex[q];
+      err[d + q] = ev[q];
+    }
+  return e;
+}
+
 /* ---------------- integration driver (Algorithm 1) ---------------- */
 
 int or_integrate(int n, const double *m, double *x, double *v, double *t, int *status,
                  double t_end, double dt, const or_params *p, double *log, int *log_count,
                  long long *kepler_iters) {
   if (n < 2 || n > MAXN || dt == 0.0 || !isfinite(dt)) return -1;
+  if (p->integrator == OR_RKCK_ADAPTIVE && !(p->rk_eps > 0.0 && isfinite(p->rk_eps))) return -1;
   if (*status >= OR_CLOSE_ENCOUNTER) return 0;
   if (p->integrator == OR_HERMITE_ADAPTIVE) {
     /* dt is tau; steps of min(Eq. 5, remaining time) toward t_end */
@@ -489,6 +569,72 @@ int or_integrate(int n, const double *m, double *x, double *v, double *t, int *s
     if (log_count) *log_count = nlog;
     return 0;
   }
+  if (p->integrator == OR_RKCK_ADAPTIVE) {
+    /* dt is the first trial step; accepted trials advance, rejected ones shrink h */
+    const double dir = dt > 0 ? 1.0 : -1.0;
+    double h = fabs(dt);
+    double rem = (t_end - *t) * dir;
+    if (!(rem > 1e-12 * fmax(1.0, fabs(t_end)))) {
+      *status = OR_DONE;
+      return 0;
+    }
+    int nlog = log_count ? *log_count : 0;
+    long long accepted = 0;
+    for (long long trial = 1; trial <= 16777216LL; trial++) {
+      rem = (t_end - *t) * dir;
+      int last = h >= rem;
+      double hs = last ? rem : h;
+      double xt[3 * MAXN], vt[3 * MAXN];
+      memcpy(xt, x, sizeof(double) * 3 * n);
+      memcpy(vt, v, sizeof(double) * 3 * n);
+      double err = or_rkck_step(n, m, xt, vt, dir * hs, NULL) / p->rk_eps;
+      if (!isfinite(err)) {
+        *status = OR_NONFINITE;
+        if (log_count) *log_count = nlog;
+        return 0;
+      }
+      if (err <= 1.0) {
+        memcpy(x, xt, sizeof(double) * 3 * n);
+        memcpy(v, vt, sizeof(double) * 3 * n);
+        *t = last ? t_end : *t + dir * hs;
+        accepted++;
+        int st = or_monitor(n, m, x, v, p->ce_factor, p->eject_radius);
+        if (st != OR_ACTIVE) {
+          *status = st;
+          if (log_count) *log_count = nlog;
+          return 0;
+        }
+        if (p->log_interval > 0 && log && accepted % p->log_interval == 0 && nlog < p->log_cap) {
+          double E, L[3];
+          or_energy(n, m, x, v, &E, L);
+          double *rec = log + 5 * nlog;
+          rec[0] = *t;
+          rec[1] = E;
+          rec[2] = L[0];
+          rec[3] = L[1];
+          rec[4] = L[2];
+          nlog++;
+        }
+        if (last) {
+          *status = OR_DONE;
+          if (log_count) *log_count = nlog;
+          return 0;
+        }
+        double f = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+        h = hs * fmin(5.0, fmax(0.2, f));
+      } else {
+        h = hs * fmax(0.2, 0.9 * pow(err, -0.2));
+      }
+      if (!(h > 0.0) || !isfinite(h) || *t + dir * h == *t) {
+        *status = OR_NONFINITE; /* step-size underflow */
+        if (log_count) *log_count = nlog;
+        return 0;
+      }
+    }
+    *status = OR_ACTIVE; /* trial cap reached before t_end */
+    if (log_count) *log_count = nlog;
+    return 0;
+  }
   double D = (t_end - *t) / dt;
   if (!(D > 1e-9)) {
     *status = OR_DONE;
@@ -507,7 +653,7 @@ int or_integrate(int n, const double *m, double *x, double *v, double *t, int *s
   } else if (p->integrator == OR_MVS_JACOBI) {
     or_inertial_to_jacobi(n, m, x, v, q, u);
     or_jacobi_interaction_acc(n, m, q, acc);
-  } else {
+  } else if (p->integrator != OR_RKCK) {
     return -1;
   }
   int nlog = log_count ? *log_count : 0;
@@ -517,6 +663,8 @@ int or_integrate(int n, const double *m, double *x, double *v, double *t, int *s
     int st = OR_ACTIVE;
     if (p->integrator == OR_HERMITE) {
       or_hermite_step(n, m, x, v, a0, j0, h, p->n_corr, p->corr_form);
+    } else if (p->integrator == OR_RKCK) {
+      or_rkck_step(n, m, x, v, h, NULL);
     } else if (p->integrator == OR_MVS_DH) {
       if (or_mvs_dh_step(n, m, q, u, acc, h)) st = OR_KEPLER_NOCONV;
       or_dh_to_inertial(n, m, q, u, x, v);
@@ -556,8 +704,9 @@ int or_integrate_ensemble(int n_sys, const int *n_body, const double *mass, doub
                           double *time, int *status, double t_end, double dt, int integrator,
                           int n_corr, int corr_form, double ce_factor, double eject_radius,
                           int log_interval, int log_cap, double *log, int *log_count,
-                          long long *kepler_iters) {
+                          long long *kepler_iters, double rk_eps) {
   or_params p;
+  p.rk_eps = rk_eps;
   p.integrator = integrator;
   p.n_corr = n_corr;
   p.corr_form = corr_form;

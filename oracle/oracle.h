@@ -21,7 +21,8 @@ extern "C" {
 enum { OR_ACTIVE = 0, OR_DONE = 1, OR_CLOSE_ENCOUNTER = 2, OR_EJECTED = 3,
        OR_KEPLER_NOCONV = 4, OR_NONFINITE = 5 };
 /* integrators */
-enum { OR_HERMITE = 1, OR_MVS_DH = 2, OR_MVS_JACOBI = 3, OR_HERMITE_ADAPTIVE = 4 };
+enum { OR_HERMITE = 1, OR_MVS_DH = 2, OR_MVS_JACOBI = 3, OR_HERMITE_ADAPTIVE = 4,
+       OR_RKCK = 5, OR_RKCK_ADAPTIVE = 6 };
 /* Hermite corrector forms: the time-symmetric form of Kokubo et al. 1998 cited in
  * Sec. 2.2.1, and the printed Eq. 4 read with 3/20 and the predicted base. */
 enum { OR_CORR_KOKUBO = 0, OR_CORR_PRINTED = 1 };
@@ -38,6 +39,18 @@ void or_hermite_step(int n, const double *m, double *x, double *v, double *a0, d
 
 /* Eq. 5: adaptive step tau * (sum_i |j_i|^2 / |a_i|^2)^(-1/2) from a0, j0 (tau > 0). */
 double or_adaptive_dt(int n, const double *a0, const double *j0, double tau);
+
+/* Runge-Kutta Cash-Karp 4(5) (Sec. 2.2.2, Sec. 4.3.3; Cash & Karp 1990).
+ * or_rkck_tableau copies out the tableau the step uses: c[6], a[6][6] (row i holds the
+ * coefficients of stage i, zero on and above the diagonal), the 5th-order weights b5[6]
+ * (the solution that is propagated) and the embedded 4th-order weights b4[6].
+ * or_rkck_step advances (x, v) by one step h of dy/dt = (v, a(x)) (Eq. 2 with Eq. 1)
+ * using six evaluations of Eq. 1, stores the 5th-order solution in x, v, writes the
+ * error vector (5th minus 4th order) to err[6n] (positions then velocities, body-major,
+ * NULL to skip), and returns the scaled error
+ *   max_b max(|ex_b| / X, |ev_b| / V),  X = max_b |x_b|, V = max_b |v_b| at the step's start. */
+void or_rkck_tableau(double *c, double *a, double *b5, double *b4);
+double or_rkck_step(int n, const double *m, double *x, double *v, double h, double *err);
 
 /* Eq. 6 energy (pairs counted once) and total angular momentum L[3]. */
 void or_energy(int n, const double *m, const double *x, const double *v, double *E, double *L);
@@ -76,11 +89,18 @@ void or_jacobi_interaction_acc(int n, const double *m, const double *r, double *
  * OR_HERMITE_ADAPTIVE takes dt as the step-size scale tau of Eq. 5 (its sign gives the
  * direction): each step is min(Eq. 5 step, distance to t_end), so the last one lands on
  * t_end; at most 2^24 steps per call, after which the system stays ACTIVE at the time
- * reached.  Systems whose status is a stop code (>= 2) are left untouched.  Every log_interval steps (0 = off)
+ * reached.  OR_RKCK takes fixed steps like OR_HERMITE.  OR_RKCK_ADAPTIVE takes dt as the
+ * first trial step: a trial whose scaled error divided by rk_eps is at most 1 is accepted
+ * (time and state advance); the next trial step is the last one times
+ * min(5, max(0.2, 0.9 err^(-1/5))) after an acceptance and max(0.2, 0.9 err^(-1/5)) after a
+ * rejection (Hairer, Norsett & Wanner, Sec. II.4); trials are clamped to land on t_end; a
+ * non-finite error or a step too small to move t stops the system as NONFINITE; at most
+ * 2^24 trials per call.  Systems whose status is a stop code (>= 2) are left untouched.  Every log_interval steps (0 = off)
  * one record (t, E, Lx, Ly, Lz) is appended to log (capacity log_cap records). */
 typedef struct {
   int integrator, n_corr, corr_form, log_interval, log_cap;
   double ce_factor, eject_radius;
+  double rk_eps;  /* error tolerance of OR_RKCK_ADAPTIVE */
 } or_params;
 int or_integrate(int n, const double *m, double *x, double *v, double *t, int *status,
                  double t_end, double dt, const or_params *p, double *log, int *log_count,
@@ -92,7 +112,7 @@ int or_integrate_ensemble(int n_sys, const int *n_body, const double *mass, doub
                           double *time, int *status, double t_end, double dt, int integrator,
                           int n_corr, int corr_form, double ce_factor, double eject_radius,
                           int log_interval, int log_cap, double *log, int *log_count,
-                          long long *kepler_iters);
+                          long long *kepler_iters, double rk_eps);
 
 #ifdef __cplusplus
 }

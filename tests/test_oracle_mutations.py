@@ -34,6 +34,11 @@ MUTANTS = {
     "jacobi_transform": ("R[c] -= m[i] / eta[i] * r[3 * i + c];", "R[c] -= m[i] / eta[i - 1] * r[3 * i + c];"),
     "adaptive_dt_square": ("s += dot3(j, j) / dot3(a, a);", "s += sqrt(dot3(j, j) / dot3(a, a));"),
     "monitor_hill_cube": ("cbrt((m[i] + m[j]) / (3.0 * m[0]))", "sqrt((m[i] + m[j]) / (3.0 * m[0]))"),
+    "rkck_b5_typo": ("125.0 / 594.0", "125.0 / 549.0"),
+    "rkck_propagate_b4": ("sx += RK_B5[s] * kx[s][q];", "sx += RK_B4[s] * kx[s][q];"),
+    "rkck_stage_velocity": ("for (int q = 0; q < d; q++) kx[s][q] = vs[q];", "for (int q = 0; q < d; q++) kx[s][q] = v[q];"),
+    "rkck_accept_loose": ("if (err <= 1.0) {", "if (err <= 100.0) {"),
+    "rkck_error_weights": ("tx += (RK_B5[s] - RK_B4[s]) * kx[s][q];", "tx += (RK_B5[s] - RK_B4[s]) * kv[s][q];"),
 }
 
 

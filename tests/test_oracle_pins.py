@@ -523,3 +523,144 @@ def test_stop_then_untouched_and_logging():
     assert out2["time"][1] == t_stop
     assert rel(out2["pos"][3:6], out["pos"][3:6]) == 0.0
     assert out2["time"][0] == 30.0
+
+
+# ----------------------------------------------------------------- Runge-Kutta Cash-Karp (Sec. 2.2.2)
+def _rk_conditions(c, A, b):
+    """Residuals of the 17 order conditions of an explicit Runge-Kutta method up to order 5
+    (one per rooted tree, Butcher 2008, Sec. 31), grouped by order."""
+    Ac = A @ c
+    Ac2 = A @ c ** 2
+    Ac3 = A @ c ** 3
+    AAc = A @ Ac
+    return {
+        1: [b.sum() - 1],
+        2: [b @ c - 1 / 2],
+        3: [b @ c ** 2 - 1 / 3, b @ Ac - 1 / 6],
+        4: [b @ c ** 3 - 1 / 4, b @ (c * Ac) - 1 / 8, b @ Ac2 - 1 / 12, b @ AAc - 1 / 24],
+        5: [b @ c ** 4 - 1 / 5, b @ (c ** 2 * Ac) - 1 / 10, b @ (c * Ac2) - 1 / 15, b @ Ac ** 2 - 1 / 20,
+            b @ (c * AAc) - 1 / 30, b @ Ac3 - 1 / 20, b @ (A @ (c * Ac)) - 1 / 40, b @ (A @ Ac2) - 1 / 60,
+            b @ (A @ AAc) - 1 / 120],
+    }
+
+
+def test_rkck_tableau_satisfies_the_order_conditions():
+    c, A, b5, b4 = O.rkck_tableau()
+    assert np.all(np.triu(A) == 0.0)  # explicit
+    assert np.abs(A.sum(axis=1) - c).max() < 1e-15  # row sums are the nodes
+    r5 = _rk_conditions(c, A, b5)
+    for order in range(1, 6):
+        assert np.abs(r5[order]).max() < 2e-15, (order, r5[order])
+    r4 = _rk_conditions(c, A, b4)
+    for order in range(1, 5):
+        assert np.abs(r4[order]).max() < 2e-15, (order, r4[order])
+    # the embedded solution is only 4th order, so the difference estimates the local error
+    assert np.abs(r4[5]).max() > 1e-4
+
+
+def rkck_two_body_error(e, N, periods=1.0):
+    m0, m1 = 1.0, 1e-3
+    mu = m0 + m1
+    T = cf.period(mu, 1.0)
+    s = ics.two_body(1.0, e, m0, m1)
+    out = O.integrate(s, periods * T, periods * T / N, O.RKCK)
+    r_ref, _ = cf.elliptic_at(mu, 1.0, e, 0.0, periods * T)
+    return np.linalg.norm(out["pos"][1] - out["pos"][0] - r_ref)
+
+
+def test_rkck_fixed_step_is_fifth_order():
+    # the propagated solution uses the 5th-order weights (local extrapolation)
+    errs = [rkck_two_body_error(0.5, N) for N in (400, 800, 1600)]
+    for a, b in zip(errs, errs[1:]):
+        assert 26.0 <= a / b <= 38.0, errs
+
+
+def test_rkck_error_vector_is_the_local_error_of_the_embedded_solution():
+    m0, m1, e = 1.0, 1e-3, 0.5
+    mu = m0 + m1
+    T = cf.period(mu, 1.0)
+    s = ics.two_body(1.0, e, m0, m1)
+    ests = []
+    for h in (T / 800, T / 1600):
+        x5, v5, scaled, err = O.rkck_step(s["mass"], s["pos"], s["vel"], h)
+        r_ref, u_ref = cf.elliptic_at(mu, 1.0, e, 0.0, h)
+        r5, u5 = x5[1] - x5[0], v5[1] - v5[0]
+        er, eu = err[1] - err[0], err[3] - err[2]
+        # 4th-order solution = 5th-order one minus the error vector
+        assert np.linalg.norm(r5 - er - r_ref) == pytest.approx(np.linalg.norm(er), rel=0.02)
+        assert np.linalg.norm(u5 - eu - u_ref) == pytest.approx(np.linalg.norm(eu), rel=0.02)
+        # the propagated 5th-order solution is one order better (error / estimate ~ h)
+        assert np.linalg.norm(r5 - r_ref) < 0.2 * np.linalg.norm(er)
+        # the scaled norm: largest body error over the largest body position / velocity
+        X = np.linalg.norm(s["pos"], axis=1).max()
+        V = np.linalg.norm(s["vel"], axis=1).max()
+        want = max(np.linalg.norm(err[:2], axis=1).max() / X, np.linalg.norm(err[2:], axis=1).max() / V)
+        assert scaled == pytest.approx(want, rel=1e-14)
+        ests.append(scaled)
+    assert 26.0 <= ests[0] / ests[1] <= 38.0  # local error O(h^5)
+
+
+def test_rkck_adaptive_meets_the_tolerance_and_lands_on_t_end():
+    m0, m1, e = 1.0, 1e-3, 0.5
+    mu = m0 + m1
+    T = cf.period(mu, 1.0)
+    r_ref, _ = cf.elliptic_at(mu, 1.0, e, 0.0, T)
+    res = {}
+    for eps in (1e-9, 1e-11):
+        s = ics.two_body(1.0, e, m0, m1)
+        out = O.integrate(s, T, 0.01, O.RKCK_ADAPTIVE, rk_eps=eps, log_interval=1, log_cap=100000)
+        assert out["time"][0] == T and out["status"][0] == O.DONE
+        steps = int(out["log_count"][0])
+        err = np.linalg.norm(out["pos"][1] - out["pos"][0] - r_ref)
+        # each accepted step's local error is at most eps times the system's scale
+        assert err <= 3.0 * steps * eps, (eps, err, steps)
+        res[eps] = (steps, err)
+    # steps grow like eps^(-1/5), the global error falls about in proportion to eps
+    ratio = res[1e-11][0] / res[1e-9][0]
+    assert 2.0 <= ratio <= 3.2, res
+    assert res[1e-11][1] < res[1e-9][1] / 20, res
+
+
+def test_rkck_adaptive_rejects_a_far_too_large_first_step():
+    m0, m1 = 1.0, 1e-3
+    s = ics.two_body(1.0, 0.3, m0, m1)
+    T = cf.period(m0 + m1, 1.0)
+    a = O.integrate(s, T / 2, 0.01, O.RKCK_ADAPTIVE, rk_eps=1e-12)
+    b = O.integrate(s, T / 2, 50.0, O.RKCK_ADAPTIVE, rk_eps=1e-12)  # 16 periods: rejected until small
+    assert a["status"][0] == b["status"][0] == O.DONE and b["time"][0] == T / 2
+    assert rel(b["pos"], a["pos"]) < 1e-9
+    # and backwards: the adaptive map integrates to an earlier time just as well
+    back = O.integrate({**s, "pos": a["pos"], "vel": a["vel"]}, 0.0, -0.01, O.RKCK_ADAPTIVE, rk_eps=1e-12,
+                       time=a["time"])
+    assert back["time"][0] == 0.0 and rel(back["pos"], s["pos"]) < 1e-9
+
+
+@pytest.mark.parametrize("L", [4.0, 0.25])
+def test_rkck_step_obeys_kepler_scaling(L):
+    # x -> L x, t -> L^(3/2) t, v -> L^(-1/2) v maps solutions of Eq. 1 (G = 1, masses fixed)
+    # onto solutions: the step, its error vector and the scaled error norm must follow
+    s = ics.three_body(1, seed=11)
+    m, x, v = s["mass"], s["pos"], s["vel"]
+    h = 0.05
+    x5, v5, e5, err = O.rkck_step(m, x, v, h)
+    xs, vs, es, errs = O.rkck_step(m, x * L, v / math.sqrt(L), h * L ** 1.5)
+    assert rel(xs, x5 * L) < 1e-13 and rel(vs, v5 / math.sqrt(L)) < 1e-13
+    assert rel(errs[:3], err[:3] * L) < 1e-9 and rel(errs[3:], err[3:] / math.sqrt(L)) < 1e-9
+    assert es == pytest.approx(e5, rel=1e-9)
+
+
+def test_rkck_adaptive_never_accepts_a_step_above_tolerance():
+    # first trial = the whole interval, with a tolerance ten times below that step's error:
+    # the trial must be rejected and the interval covered by smaller accepted steps
+    m0, m1, e = 1.0, 1e-3, 0.5
+    mu = m0 + m1
+    T = cf.period(mu, 1.0)
+    s = ics.two_body(1.0, e, m0, m1)
+    h = T / 50
+    _, _, big, _ = O.rkck_step(s["mass"], s["pos"], s["vel"], h)
+    eps = big / 10
+    out = O.integrate(s, h, h, O.RKCK_ADAPTIVE, rk_eps=eps, log_interval=1, log_cap=1000)
+    steps = int(out["log_count"][0])
+    assert out["time"][0] == h and steps >= 2
+    r_ref, _ = cf.elliptic_at(mu, 1.0, e, 0.0, h)
+    assert np.linalg.norm(out["pos"][1] - out["pos"][0] - r_ref) <= 3.0 * steps * eps
