@@ -63,7 +63,9 @@ def source_hash(patterns):
     return h.hexdigest()[:16]
 
 
-HERMITE_SOURCES = ["paper_1208_1157_gb300/csrc/hermite*.cu*", "paper_1208_1157_gb300/csrc/common.cuh"]
+# the sources of the benchmark's kernel (hermite_uniform_kernel, system per lane)
+HERMITE_SOURCES = ["paper_1208_1157_gb300/csrc/hermite.cuh", "paper_1208_1157_gb300/csrc/hermite_impl.cuh",
+                   "paper_1208_1157_gb300/csrc/hermite_uniform_spl.cu", "paper_1208_1157_gb300/csrc/common.cuh"]
 
 
 def traffic_per_launch(kernel, systems):
@@ -249,6 +251,12 @@ def secondary(S, torch, stream):
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
     out["c4_mvs_dh_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20)
+    out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
+    out["c2_rkck_fixed_500"] = timed(c2, 500 * DT, S.RKCK, DT)
+    out["c2_rkck_adaptive_eps_1e-12_one_period"] = timed(c2, TWO_PI, S.RKCK_ADAPTIVE, 0.05)
+    out["c3_ragged_rkck_4_steps"] = timed(c3, 4 * DT, S.RKCK, DT)
+    c6 = ics.ragged_wide(16384, seed=6)
+    out["wide_16_to_32_bodies_hermite_20_steps"] = timed(c6, 20 * DT, S.HERMITE4, DT)
     out["serving"] = serving(S, stream)
     return out
 
@@ -454,6 +462,12 @@ def ncu_case(name):
     elif name == "ragged":
         ens = ics.ragged(65536, seed=3)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 2, S.HERMITE4, DT
+    elif name == "rkck":
+        ens = ics.three_body(N_SYS, seed=2)
+        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 50, S.RKCK, DT
+    elif name == "wide":
+        ens = ics.ragged_wide(16384, seed=6)
+        mapping, steps, integ, dt = S.MAP_AUTO, 10, S.HERMITE4, DT
     else:
         raise SystemExit(f"unknown case {name}")
     with S.Ensemble(ens, stream=stream) as e:
@@ -474,7 +488,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged"])
+    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged", "rkck", "wide"])
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)

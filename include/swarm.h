@@ -1,12 +1,14 @@
 /*
  * swarm.h — C ABI of a GB300 (sm_103a) library that advances large ensembles of
- * independent few-body gravitational systems (2..15 bodies each) in FP64, with the
- * two integrators of Swarm-NG (Dindar et al., arXiv:1208.1157):
+ * independent few-body gravitational systems (2..32 bodies each) in FP64, with the
+ * integrators of Swarm-NG (Dindar et al., arXiv:1208.1157):
  *   - the 4th-order time-symmetric Hermite predict-evaluate-correct step (Sec. 2.2.1,
  *     Eq. 3 predictor, Eq. 4 corrector read in the time-symmetric form of Kokubo et
  *     al. 1998, Algorithm 2, two corrector passes, three force evaluations per step);
+ *   - the same with the adaptive step of Eq. 5 (Sec. 4.3.2);
  *   - the mixed-variable symplectic step (Sec. 2.2.3, Sec. 4.3.4) in democratic
- *     heliocentric or Jacobi coordinates, with a universal-variable Kepler drift.
+ *     heliocentric or Jacobi coordinates, with a universal-variable Kepler drift;
+ *   - the Runge-Kutta Cash-Karp 4(5) step, fixed or adaptive (Sec. 2.2.2, Sec. 4.3.3).
  * The multi-step loop runs on the device (Algorithm 1, Sec. 5.3): one call advances
  * every system to t_end with a monitor after each step.
  *
@@ -48,10 +50,21 @@ enum swarm_integrator {
   SWARM_HERMITE4 = 1,          /* Sec. 2.2.1 / Algorithm 2 */
   SWARM_MVS_DH = 2,            /* Sec. 2.2.3, democratic heliocentric, five sub-steps */
   SWARM_MVS_JACOBI = 3,        /* Wisdom & Holman 1991 map in Jacobi coordinates */
-  SWARM_HERMITE4_ADAPTIVE = 4  /* Hermite with the step of Eq. 5, dt = tau (sum |j|^2/|a|^2)^(-1/2) from
+  SWARM_HERMITE4_ADAPTIVE = 4, /* Hermite with the step of Eq. 5, dt = tau (sum |j|^2/|a|^2)^(-1/2) from
                                   the start of each step; swarm_integrate's dt is tau (its sign is the
                                   direction); the last step lands on t_end; at most 2^24 steps per call
                                   and system (a system short of t_end then stays ACTIVE) */
+  SWARM_RKCK = 5,              /* Runge-Kutta Cash-Karp 4(5) (Sec. 2.2.2, Sec. 4.3.3), fixed steps: six
+                                  force evaluations per step, the 5th-order solution propagated */
+  SWARM_RKCK_ADAPTIVE = 6      /* same, adaptive: swarm_integrate's dt is the first trial step (its sign
+                                  the direction); a trial is accepted when max over bodies of
+                                  max(|err_x|/X, |err_v|/V) <= the tolerance (swarm_set_tolerance), X and
+                                  V the system's largest body position and speed at the step's start,
+                                  err the difference of the 5th- and 4th-order solutions; the next trial
+                                  is h * min(5, max(0.2, 0.9 err^(-1/5))) (after a rejection at most
+                                  0.9 h); the last step lands on t_end; at most 2^24 trials per call and
+                                  system (a system short of t_end then stays ACTIVE); a step too small to
+                                  advance the time stops the system as NONFINITE */
 };
 
 /* per-system status (the monitor of Sec. 4.3, Algorithm 1) */
@@ -102,7 +115,9 @@ typedef struct {
 
 /* ------------------------------------------------------------------ ensembles */
 /* Create an ensemble of n_sys systems and upload its initial state (host arrays).
- * n_body[s] in 2..15; mass > 0 and finite; pos/vel finite; time of every system t0.
+ * n_body[s] in 2..32 (systems of more than 15 bodies are integrated by the Hermite
+ * integrators only: one system per warp); mass > 0 and finite; pos/vel finite; time of
+ * every system t0.
  * cuda_stream: a cudaStream_t to run on (NULL = the legacy default stream).
  * Returns SWARM_EINVAL for bad sizes/values, SWARM_ENOMEM, SWARM_ECUDA. */
 int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const double *mass, const double *pos,
@@ -115,6 +130,10 @@ int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const double *ma
 int swarm_set_stop(swarm_ensemble *ens, double ce_hill_factor, double eject_radius);
 
 int swarm_set_option(swarm_ensemble *ens, int option, int64_t value);
+
+/* Error tolerance of SWARM_RKCK_ADAPTIVE (Sec. 4.3.3, "error tolerance"), 0 < eps < 1;
+ * default 1e-12.  SWARM_EINVAL outside that range. */
+int swarm_set_tolerance(swarm_ensemble *ens, double eps);
 
 /* Advance every runnable system (status ACTIVE or DONE) from its own time to t_end with
  * step dt (negative when t_end is earlier).  Step count per system: N = round(D) when
@@ -143,6 +162,21 @@ int swarm_query_diagnostics(const swarm_ensemble *ens, double *energy, double *a
  * `records` in records; *count gets the number written. */
 int swarm_query_log(const swarm_ensemble *ens, int32_t sys, double *records, int32_t cap, int32_t *count);
 int swarm_query_stats(const swarm_ensemble *ens, swarm_stats *out);
+
+/* Radial-velocity observable (the on-device data reduction of Sec. 4.4, for the
+ * radial-velocity fitting of Sec. 6).  los[3] is a unit vector pointing from the observer
+ * to the systems (|los| = 1 within 1e-12, else SWARM_EINVAL); the radial velocity of a
+ * system is its central body's velocity along it, v_0 . los (positive = receding), in
+ * the ensemble's inertial frame.
+ * swarm_query_rv: at the current state, rv[n_sys] (host); one double per system moves.
+ * swarm_observe_rv: for k = 0..n_obs-1 integrate to t_obs[k] (as swarm_integrate with
+ * this integrator and dt; the times must run in the direction of dt) and record the
+ * radial velocities on the device; rv[n_obs][n_sys] (host) is copied once at the end.
+ * A system that stops keeps its state, so its later records repeat its value at the stop
+ * (the status array tells).  swarm_query_stats then describes the last interval. */
+int swarm_query_rv(const swarm_ensemble *ens, const double *los, double *rv);
+int swarm_observe_rv(swarm_ensemble *ens, const double *t_obs, int32_t n_obs, int integrator, double dt,
+                     const double *los, double *rv);
 int32_t swarm_ensemble_size(const swarm_ensemble *ens);
 void swarm_destroy_ensemble(swarm_ensemble *ens);
 

@@ -79,6 +79,9 @@ def _declare(L):
                                         C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _dp, _ip,
                                         C.POINTER(C.c_longlong), C.c_double]
     L.or_integrate_ensemble.restype = C.c_int
+    L.or_observe_rv_ensemble.argtypes = [C.c_int, _ip, _dp, _dp, _dp, _dp, _ip, _dp, C.c_int, C.c_double, C.c_int,
+                                         C.c_double, C.c_double, C.c_double, _dp, _dp]
+    L.or_observe_rv_ensemble.restype = C.c_int
     L.or_rkck_tableau.argtypes = [_dp, _dp, _dp, _dp]
     L.or_rkck_step.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, _dp]
     L.or_rkck_step.restype = C.c_double
@@ -229,3 +232,25 @@ def integrate(ens: dict, t_end: float, dt: float, integrator: int = HERMITE, n_c
         raise ValueError(f"oracle integrate rejected its arguments (rc={rc})")
     return {"pos": pos, "vel": vel, "time": tm, "status": stt, "log": log[:, :cap], "log_count": cnt,
             "kepler_iters": kit.value}
+
+
+def observe_rv(ens: dict, t_obs, dt: float, integrator: int = HERMITE, los=(0.0, 0.0, 1.0), ce_factor: float = 0.0,
+               eject_radius: float = 0.0, rk_eps: float = 1e-12) -> dict:
+    """Radial velocity of every system's central body at each observation time:
+    rv [n_obs][n_sys], plus the final state."""
+    n_body = np.ascontiguousarray(ens["n_body"], dtype=np.int32)
+    S = len(n_body)
+    mass = _f64(ens["mass"])
+    pos = _f64(ens["pos"], (-1, 3))
+    vel = _f64(ens["vel"], (-1, 3))
+    tm = np.zeros(S)
+    stt = np.zeros(S, dtype=np.int32)
+    t_obs = _f64(t_obs)
+    los = _f64(los)
+    rv = np.zeros((len(t_obs), S))
+    rc = lib().or_observe_rv_ensemble(S, n_body.ctypes.data_as(_ip), _d(mass), _d(pos), _d(vel), _d(tm),
+                                      stt.ctypes.data_as(_ip), _d(t_obs), len(t_obs), float(dt), int(integrator),
+                                      float(ce_factor), float(eject_radius), float(rk_eps), _d(los), _d(rv))
+    if rc != 0:
+        raise ValueError(f"oracle observe_rv rejected its arguments (rc={rc})")
+    return {"rv": rv, "pos": pos, "vel": vel, "time": tm, "status": stt}

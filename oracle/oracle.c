@@ -726,3 +726,39 @@ int or_integrate_ensemble(int n_sys, const int *n_body, const double *mass, doub
   }
   return 0;
 }
+
+/* ---------------- radial-velocity observable (Sec. 4.4 data reduction, Sec. 6 use) ---------------- */
+int or_observe_rv(int n, const double *m, double *x, double *v, double *t, int *status, const double *t_obs,
+                  int n_obs, double dt, const or_params *p, const double *los, double *rv) {
+  for (int k = 0; k < n_obs; k++) {
+    int rc = or_integrate(n, m, x, v, t, status, t_obs[k], dt, p, NULL, NULL, NULL);
+    if (rc) return rc;
+    rv[k] = v[0] * los[0] + v[1] * los[1] + v[2] * los[2];
+  }
+  return 0;
+}
+
+int or_observe_rv_ensemble(int n_sys, const int *n_body, const double *mass, double *pos, double *vel,
+                           double *time, int *status, const double *t_obs, int n_obs, double dt, int integrator,
+                           double ce_factor, double eject_radius, double rk_eps, const double *los, double *rv) {
+  or_params p;
+  p.integrator = integrator;
+  p.n_corr = 2;
+  p.corr_form = OR_CORR_KOKUBO;
+  p.log_interval = 0;
+  p.log_cap = 0;
+  p.ce_factor = ce_factor;
+  p.eject_radius = eject_radius;
+  p.rk_eps = rk_eps;
+  double col[4096];
+  if (n_obs > 4096) return -1;
+  long long off = 0;
+  for (int s = 0; s < n_sys; s++) {
+    int rc = or_observe_rv(n_body[s], mass + off, pos + 3 * off, vel + 3 * off, time + s, status + s, t_obs, n_obs,
+                           dt, &p, los, col);
+    if (rc) return rc;
+    for (int k = 0; k < n_obs; k++) rv[(long long)k * n_sys + s] = col[k];
+    off += n_body[s];
+  }
+  return 0;
+}

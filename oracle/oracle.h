@@ -106,6 +106,18 @@ int or_integrate(int n, const double *m, double *x, double *v, double *t, int *s
                  double t_end, double dt, const or_params *p, double *log, int *log_count,
                  long long *kepler_iters);
 
+/* Radial velocity of the central body for radial-velocity fitting (the data reduction of
+ * Sec. 4.4 applied to the use of Sec. 6): for k = 0..n_obs-1 integrate to t_obs[k] with
+ * or_integrate, then rv[k] = v_0 . los (los: unit vector from the observer to the system,
+ * so a receding star has rv > 0).  A stopped system keeps its state, so its later records
+ * repeat the value at the stop. */
+int or_observe_rv(int n, const double *m, double *x, double *v, double *t, int *status, const double *t_obs,
+                  int n_obs, double dt, const or_params *p, const double *los, double *rv);
+int or_observe_rv_ensemble(int n_sys, const int *n_body, const double *mass, double *pos, double *vel,
+                           double *time, int *status, const double *t_obs, int n_obs, double dt, int integrator,
+                           double ce_factor, double eject_radius, double rk_eps, const double *los,
+                           double *rv /* [n_obs][n_sys] */);
+
 /* Ensemble wrapper: systems back to back (n_body[s] bodies each).  log is
  * [n_sys][log_cap][5], log_count [n_sys]; either may be NULL when log_interval = 0. */
 int or_integrate_ensemble(int n_sys, const int *n_body, const double *mass, double *pos, double *vel,

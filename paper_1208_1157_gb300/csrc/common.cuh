@@ -6,8 +6,14 @@
 
 #include "../../include/swarm.h"
 
-#define SWARM_MAX_N 15
+#define SWARM_MAX_N 32   // largest body count of an ensemble
 #define SWARM_MIN_N 2
+#define SWARM_RING_MAX_N 15  // largest n of the per-n compiled kernels (all integrators, server)
+
+namespace swarm {
+constexpr int kWideMinN = SWARM_RING_MAX_N + 1;  // 16..32: one system per warp, run-time n
+constexpr int kMapWide = 4;                      // internal mapping code of those bins
+}
 
 namespace swarm {
 
@@ -39,6 +45,7 @@ struct StepParams {
   int *work_next;        // dynamic work-list head (persistent multi-bin launch)
   int max_steps = 0;     // cap on the steps one launch takes per system (0: none)
   const double *t_end_dev = nullptr;  // end time read from device memory (graph replays)
+  double rk_eps = 1e-12;  // error tolerance of the adaptive Runge-Kutta Cash-Karp step
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }

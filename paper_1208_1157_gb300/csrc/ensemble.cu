@@ -88,6 +88,7 @@ struct swarm_ensemble {
   int mapping = SWARM_MAP_AUTO, n_corr = 2, steps_per_launch = 0, single_launch = 1, ctas_per_sm = 0;
   int corr_form = 0;
   double ce = 0.0, eject = 0.0;
+  double rk_eps = 1e-12;  // adaptive Runge-Kutta tolerance
   double t_lo = 0.0, t_hi = 0.0;  // range of runnable systems' times (step-count guard)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // chunked launches (SWARM_OPT_STEPS_PER_LAUNCH): captured once, replayed
@@ -336,6 +337,13 @@ extern "C" int swarm_set_stop(swarm_ensemble *e, double ce, double ej) {
   return SWARM_OK;
 }
 
+extern "C" int swarm_set_tolerance(swarm_ensemble *e, double eps) {
+  if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");
+  if (!(eps > 0.0 && eps < 1.0)) return fail(SWARM_EINVAL, "tolerance must be in (0, 1)");
+  e->rk_eps = eps;
+  return SWARM_OK;
+}
+
 extern "C" int swarm_set_option(swarm_ensemble *e, int option, int64_t value) {
   if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");
   switch (option) {
@@ -399,7 +407,7 @@ static int sm_count() {
 }
 
 static int units_of(int n, int S, int mapping) {
-  int per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : 32 / n;
+  int per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : (mapping == kMapWide ? 1 : 32 / n);
   return (S + per - 1) / per;
 }
 
@@ -409,6 +417,7 @@ static int build_work(swarm_ensemble *e, const std::vector<int> &maps) {
   if (e->d_work && maps == e->work_key) return SWARM_OK;
   std::vector<int4> w;
   for (size_t i = 0; i < e->bins.size(); i++) {
+    if (maps[i] == kMapWide) continue;  // 16..32-body bins run in their own launches
     int u = units_of(e->bins[i].n, e->bins[i].S, maps[i]);
     for (int k = 0; k < u; k++) w.push_back(make_int4((int)i, k, maps[i], e->bins[i].n));
   }
@@ -440,6 +449,7 @@ static StepParams make_params(swarm_ensemble *e, double t_end, int integrator, d
   P.log_count = e->d_log_count;
   P.counters = e->d_counters;
   P.work_next = e->d_work_next;
+  P.rk_eps = e->rk_eps;
   return P;
 }
 
@@ -534,12 +544,22 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
 static bool hermite_family(int integrator) {
   return integrator == SWARM_HERMITE4 || integrator == SWARM_HERMITE4_ADAPTIVE;
 }
+static bool rkck_family(int integrator) { return integrator == SWARM_RKCK || integrator == SWARM_RKCK_ADAPTIVE; }
+// adaptive integrators: the step count is not known in advance (one launch per call)
+static bool adaptive(int integrator) {
+  return integrator == SWARM_HERMITE4_ADAPTIVE || integrator == SWARM_RKCK_ADAPTIVE;
+}
 
 static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator) {
   std::vector<int> maps(e->bins.size()), bin_ctas(e->bins.size(), e->ctas_per_sm);
   int ctas = e->ctas_per_sm;
   for (size_t i = 0; i < e->bins.size(); i++) {
     int m = e->mapping;
+    if (rkck_family(integrator)) m = SWARM_MAP_BODY_PER_LANE;  // the only Runge-Kutta mapping
+    if (e->bins[i].n >= kWideMinN) {  // one system per warp, run-time n
+      maps[i] = kMapWide;
+      continue;
+    }
     if (m == SWARM_MAP_AUTO) {
       int32_t mm = SWARM_MAP_BODY_PER_LANE, cc = 0;
       // the adaptive Hermite shares the fixed-step Hermite's tuning (same kernels per step)
@@ -556,9 +576,12 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   }
   int rc = build_work(e, maps);
   if (rc) return rc;
+  std::vector<int> wide;  // bins of 16..32 bodies
+  for (size_t i = 0; i < e->bins.size(); i++)
+    if (maps[i] == kMapWide) wide.push_back((int)i);
   // one launch over every bin (the cost-ordered work list), or one single-bin kernel per bin
   // (body inlined, registers sized for that n) when there is one bin or the option asks
-  const bool per_bin = e->bins.size() == 1 || !e->single_launch;
+  const bool per_bin = e->bins.size() - wide.size() <= 1 || !e->single_launch || rkck_family(integrator);
   const int sms = sm_count();
   struct Uni {
     BinView view;
@@ -574,7 +597,9 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = units_of(u.view.n, u.view.S, u.mapping);
       int blocks = 0;
       u.variant = bin_ctas[i] == 3 ? 1 : 0;
-      if (hermite_family(integrator)) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
+      if (u.mapping == kMapWide) CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
+      else if (hermite_family(integrator)) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
+      else if (rkck_family(integrator)) CK(launch_rkck_uniform(u.view, u.nunits, P, 0, e->stream, &blocks));
       else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, P, 0, e->stream, &blocks));
       if (blocks <= 0) return fail(SWARM_ECUDA, "single-bin kernel cannot be resident");
       int c = (bin_ctas[i] && bin_ctas[i] < blocks) ? bin_ctas[i] : blocks;
@@ -582,31 +607,51 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       uni.push_back(u);
     }
   } else {
+    for (int i : wide) {  // the wide bins keep single-bin launches next to the shared one
+      Uni u;
+      u.view = e->bins[i].view();
+      u.mapping = kMapWide;
+      u.nunits = u.view.S;
+      u.variant = 0;
+      int blocks = 0;
+      CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
+      if (blocks <= 0) return fail(SWARM_ECUDA, "wide kernel cannot be resident");
+      u.grid = std::max(1, std::min(sms * blocks, (u.nunits + 3) / 4));
+      uni.push_back(u);
+    }
     int maxb = hermite_family(integrator) ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
     if (maxb <= 0) return fail(SWARM_ECUDA, "persistent kernel cannot be resident");
     if (!ctas || ctas > maxb) ctas = maxb;
     grid = std::max(1, std::min(sms * ctas, (e->nwork + 3) / 4));
   }
   auto enqueue = [&](cudaStream_t cs, const StepParams &Q) -> int {
-    if (per_bin) {
-      for (size_t i = 0; i < uni.size(); i++) {
-        StepParams Qi = Q;
-        Qi.work_next = e->d_work_next + i;
-        CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), cs));
-        if (hermite_family(integrator))
-          CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr, uni[i].variant));
-        else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr));
-      }
-    } else {
+    // single-bin launches (every bin, or only the wide bins next to the shared launch),
+    // each with its own work counter after the shared launch's
+    for (size_t i = 0; i < uni.size(); i++) {
+      StepParams Qi = Q;
+      Qi.work_next = e->d_work_next + 1 + i;
+      CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), cs));
+      if (uni[i].mapping == kMapWide)
+        CK(launch_hermite_wide(uni[i].view, Qi, uni[i].grid, cs, nullptr));
+      else if (hermite_family(integrator))
+        CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr,
+                                  uni[i].variant));
+      else if (rkck_family(integrator))
+        CK(launch_rkck_uniform(uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr));
+      else
+        CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs,
+                              nullptr));
+    }
+    if (!per_bin) {
       CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
       if (hermite_family(integrator)) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
       else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
     }
     return SWARM_OK;
   };
-  const int per_call = per_bin ? (int)uni.size() : 1;
+  const int per_call = (int)uni.size() + (per_bin ? 0 : 1);
   // the adaptive step count is not known in advance: always one launch per call
-  if (e->steps_per_launch <= 0 || integrator == SWARM_HERMITE4_ADAPTIVE) {
+  if (e->steps_per_launch <= 0 || adaptive(integrator)) {
     if ((rc = enqueue(e->stream, P))) return rc;
     e->launches += per_call;
     return SWARM_OK;
@@ -641,14 +686,18 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
 
 static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, double dt, bool sync) {
   if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");
-  if (integrator != SWARM_HERMITE4 && integrator != SWARM_MVS_DH && integrator != SWARM_MVS_JACOBI &&
-      integrator != SWARM_HERMITE4_ADAPTIVE)
+  if (integrator < SWARM_HERMITE4 || integrator > SWARM_RKCK_ADAPTIVE)
     return fail(SWARM_EINVAL, "unknown integrator %d", integrator);
   if (!(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t_end)) return fail(SWARM_EINVAL, "dt must be finite and non-zero, t_end finite");
   double span = std::max(std::fabs(t_end - e->t_lo), std::fabs(t_end - e->t_hi)) / std::fabs(dt);
-  if (integrator != SWARM_HERMITE4_ADAPTIVE && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
+  if (!adaptive(integrator) && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
   if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && (integrator != SWARM_HERMITE4 || e->corr_form))
     return fail(SWARM_EINVAL, "the plain per-step baseline exists for the fixed-step time-symmetric Hermite only");
+  if (!hermite_family(integrator))
+    for (auto &b : e->bins)
+      if (b.n > SWARM_RING_MAX_N)
+        return fail(SWARM_EINVAL, "systems of more than %d bodies are integrated by the Hermite integrators only",
+                    SWARM_RING_MAX_N);
   StepParams P = make_params(e, t_end, integrator, dt);
   CK(cudaMemsetAsync(e->d_counters, 0, sizeof(unsigned long long) * 4, e->stream));
   e->launches = 0;
@@ -658,7 +707,7 @@ static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, doubl
   CK(cudaEventRecord(e->ev1, e->stream));
   e->last_integrator = integrator;
   e->stats_pending = true;
-  if (integrator != SWARM_HERMITE4_ADAPTIVE) {
+  if (!adaptive(integrator)) {
     e->t_lo = e->t_hi = t_end;  // every runnable system ends at t_end (stopped ones never run again)
   } else {  // an adaptive call may stop short of t_end (step cap)
     e->t_lo = std::min(e->t_lo, t_end);
@@ -742,6 +791,70 @@ extern "C" int swarm_query_diagnostics(const swarm_ensemble *e, double *energy, 
     if (angmom)
       for (int c = 0; c < 3; c++) angmom[3 * s + c] = d[4 * s + 1 + c];
   }
+  return SWARM_OK;
+}
+
+// v_0 . los of every system of a bin (radial velocity of the central body)
+__global__ void rv_kernel(BinView B, double l0, double l1, double l2, double *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.S) return;
+  const int n = B.n, SP = B.S_pad;
+  const double vx = B.v[(size_t)(0 * n) * SP + s], vy = B.v[(size_t)(1 * n) * SP + s],
+               vz = B.v[(size_t)(2 * n) * SP + s];
+  out[B.gidx[s]] = vx * l0 + vy * l1 + vz * l2;
+}
+
+static int check_los(const double *los) {
+  if (!los || !std::isfinite(los[0]) || !std::isfinite(los[1]) || !std::isfinite(los[2]))
+    return fail(SWARM_EINVAL, "line of sight must be three finite numbers");
+  const double nn = los[0] * los[0] + los[1] * los[1] + los[2] * los[2];
+  if (std::fabs(nn - 1.0) > 1e-12) return fail(SWARM_EINVAL, "line of sight must be a unit vector");
+  return SWARM_OK;
+}
+
+static int enqueue_rv(const swarm_ensemble *e, const double *los, double *d_out) {
+  for (auto &b : e->bins) {
+    rv_kernel<<<(b.S + 127) / 128, 128, 0, e->stream>>>(b.view(), los[0], los[1], los[2], d_out);
+    CK(cudaGetLastError());
+  }
+  return SWARM_OK;
+}
+
+extern "C" int swarm_query_rv(const swarm_ensemble *e, const double *los, double *rv) {
+  if (!e || !rv) return fail(SWARM_EINVAL, "NULL argument");
+  int rc = check_los(los);
+  if (rc) return rc;
+  if ((rc = enqueue_rv(e, los, e->stage_diag()))) return rc;
+  CK(cudaMemcpyAsync(rv, e->stage_diag(), sizeof(double) * e->n_sys, cudaMemcpyDeviceToHost, e->stream));
+  CK(cudaStreamSynchronize(e->stream));
+  return SWARM_OK;
+}
+
+extern "C" int swarm_observe_rv(swarm_ensemble *e, const double *t_obs, int32_t n_obs, int integrator, double dt,
+                                const double *los, double *rv) {
+  if (!e || !t_obs || !rv) return fail(SWARM_EINVAL, "NULL argument");
+  if (n_obs < 1) return fail(SWARM_EINVAL, "n_obs must be at least 1");
+  int rc = check_los(los);
+  if (rc) return rc;
+  for (int k = 0; k < n_obs; k++) {
+    if (!std::isfinite(t_obs[k])) return fail(SWARM_EINVAL, "t_obs[%d] is not finite", k);
+    if (k > 0 && (t_obs[k] - t_obs[k - 1]) * dt < 0.0)
+      return fail(SWARM_EINVAL, "observation times must run in the direction of dt");
+  }
+  double *d_rec = nullptr;
+  CK(cudaMalloc(&d_rec, sizeof(double) * (size_t)n_obs * e->n_sys));
+  for (int k = 0; k < n_obs && rc == SWARM_OK; k++) {
+    rc = integrate_impl(e, t_obs[k], integrator, dt, false);
+    if (rc == SWARM_OK) rc = enqueue_rv(e, los, d_rec + (size_t)k * e->n_sys);
+  }
+  cudaError_t ce = cudaSuccess;
+  if (rc == SWARM_OK)
+    ce = cudaMemcpyAsync(rv, d_rec, sizeof(double) * (size_t)n_obs * e->n_sys, cudaMemcpyDeviceToHost, e->stream);
+  cudaError_t se = cudaStreamSynchronize(e->stream);
+  cudaFree(d_rec);
+  if (rc) return rc;
+  CK(ce);
+  CK(se);
   return SWARM_OK;
 }
 

@@ -32,6 +32,28 @@ cudaError_t launch_hermite_uniform(int mapping, const BinView &B, int nunits, co
 cudaError_t launch_mvs_uniform(bool jacobi, const BinView &B, int nunits, const StepParams &P, int grid,
                                cudaStream_t st, int *blocks);
 
+// Runge-Kutta Cash-Karp single-bin kernels (body per lane), fixed or adaptive steps.
+cudaError_t launch_rkck_fixed_a(int n, const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
+                                int *blocks);
+cudaError_t launch_rkck_fixed_b(int n, const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
+                                int *blocks);
+cudaError_t launch_rkck_adaptive_a(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                   cudaStream_t st, int *blocks);
+cudaError_t launch_rkck_adaptive_b(int n, const BinView &B, int nunits, const StepParams &P, int grid,
+                                   cudaStream_t st, int *blocks);
+inline cudaError_t launch_rkck_uniform(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
+                                       int *blocks) {
+  const bool ad = P.integrator == SWARM_RKCK_ADAPTIVE;
+  if (B.n <= 8)
+    return ad ? launch_rkck_adaptive_a(B.n, B, nunits, P, grid, st, blocks)
+              : launch_rkck_fixed_a(B.n, B, nunits, P, grid, st, blocks);
+  return ad ? launch_rkck_adaptive_b(B.n, B, nunits, P, grid, st, blocks)
+            : launch_rkck_fixed_b(B.n, B, nunits, P, grid, st, blocks);
+}
+
+// Hermite for 16..32-body bins: one system per warp (work unit = system).
+cudaError_t launch_hermite_wide(const BinView &B, const StepParams &P, int grid, cudaStream_t st, int *blocks);
+
 void set_last_error(const char *msg);
 
 cudaError_t launch_fp64_peak(double *out, long long iters, int grid, int block, cudaStream_t st);

@@ -51,7 +51,7 @@ extern "C" int swarm_hermite_integrate_noalloc(int32_t n, int32_t n_sys, int32_t
                                                const double *d_m, double *d_t, int32_t *d_status, double t_end,
                                                double dt, double ce_hill_factor, double eject_radius,
                                                void *cuda_stream) {
-  if (n < SWARM_MIN_N || n > SWARM_MAX_N) return reject(SWARM_EINVAL, "n must be in 2..15");
+  if (n < SWARM_MIN_N || n > SWARM_RING_MAX_N) return reject(SWARM_EINVAL, "n must be in 2..15");
   if (n_sys < 1 || s_pad < n_sys) return reject(SWARM_EINVAL, "need 1 <= n_sys <= s_pad");
   if (!d_x || !d_v || !d_m || !d_t || !d_status) return reject(SWARM_EINVAL, "NULL device array");
   if (!(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t_end) || !std::isfinite(ce_hill_factor) ||

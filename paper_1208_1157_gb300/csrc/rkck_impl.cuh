@@ -1,0 +1,320 @@
+// Runge-Kutta Cash-Karp 4(5) (Sec. 2.2.2, Sec. 4.3.3) on sm_103a, body per lane.
+//
+// y = (x, v), dy/dt = (v, a(x)) with a from Eq. 1 (acceleration only, no jerk).  Six
+// stages per step; the 5th-order solution is propagated and the difference to the
+// embedded 4th-order solution is the error estimate of the adaptive version.  The
+// acceleration at the accepted state is the next step's first stage and gives the
+// monitor its pair distances, so a step costs six force evaluations.
+//
+// Lane b of a group holds body b: its stage velocities and accelerations stay in
+// registers (11 vectors); pair terms are exchanged with warp shuffles (ring_acc).
+#pragma once
+#include "mvs_impl.cuh"
+
+namespace swarm {
+
+// The embedded pair of Cash & Karp, ACM TOMS 16 (1990) 201: stage coefficients A, the
+// 5th-order weights B5 and the differences E = B5 - B4 to the 4th-order weights.
+struct CK {
+  static constexpr double A21 = 1.0 / 5.0;
+  static constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+  static constexpr double A41 = 3.0 / 10.0, A42 = -9.0 / 10.0, A43 = 6.0 / 5.0;
+  static constexpr double A51 = -11.0 / 54.0, A52 = 5.0 / 2.0, A53 = -70.0 / 27.0, A54 = 35.0 / 27.0;
+  static constexpr double A61 = 1631.0 / 55296.0, A62 = 175.0 / 512.0, A63 = 575.0 / 13824.0,
+                          A64 = 44275.0 / 110592.0, A65 = 253.0 / 4096.0;
+  static constexpr double B1 = 37.0 / 378.0, B3 = 250.0 / 621.0, B4 = 125.0 / 594.0, B6 = 512.0 / 1771.0;
+  static constexpr double E1 = 37.0 / 378.0 - 2825.0 / 27648.0, E3 = 250.0 / 621.0 - 18575.0 / 48384.0,
+                          E4 = 125.0 / 594.0 - 13525.0 / 55296.0, E5 = -277.0 / 14336.0,
+                          E6 = 512.0 / 1771.0 - 1.0 / 4.0;
+};
+
+constexpr int kRkckTrialCap = 1 << 24;
+
+// group maximum of non-negative values, broadcast to every lane of the group
+template <int N>
+__device__ __forceinline__ double grp_max(double val, int b, int base) {
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, val, off);
+    if (b + off < N) val = fmax(val, o);
+  }
+  return shfl(val, base);
+}
+
+// err^(-1/5) to FP64 accuracy: a single-precision estimate refined by one Newton step on
+// y^-5 = err (y <- y (6 - err y^5) / 5); err in [1e-30, 1e30].
+__device__ __forceinline__ double inv_fifth_root(double err) {
+  const float yf = exp2f(-0.2f * log2f((float)err));
+  double y = (double)yf;
+  const double y2 = y * y;
+  const double y5 = y2 * y2 * y;
+  return y * fma(-err, y5, 6.0) * 0.2;
+}
+
+// One Cash-Karp step of length h from (x, v) with first-stage acceleration a1: writes
+// the 5th-order solution and, when E is true, the error vector (5th minus 4th order).
+template <int N, bool E>
+__device__ __forceinline__ void rkck_stages(const double (&x)[3], const double (&v)[3], const double (&a1)[3],
+                                            double m, int b, int base, double h, double (&x5)[3], double (&v5)[3],
+                                            double (&ex)[3], double (&ev)[3]) {
+  constexpr int RT = ARing<N>::RTA;
+  double d2[RT];
+  double v2[3], v3[3], v4[3], v5s[3], v6[3];
+  double a2[3], a3[3], a4[3], a5[3], a6[3];
+  double xs[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    xs[c] = fma(h, CK::A21 * v[c], x[c]);
+    v2[c] = fma(h, CK::A21 * a1[c], v[c]);
+  }
+  ring_acc<N, 0>(xs, m, b, base, a2, d2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    xs[c] = fma(h, fma(CK::A32, v2[c], CK::A31 * v[c]), x[c]);
+    v3[c] = fma(h, fma(CK::A32, a2[c], CK::A31 * a1[c]), v[c]);
+  }
+  ring_acc<N, 0>(xs, m, b, base, a3, d2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], CK::A41 * v[c])), x[c]);
+    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], CK::A41 * a1[c])), v[c]);
+  }
+  ring_acc<N, 0>(xs, m, b, base, a4, d2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], CK::A51 * v[c]))), x[c]);
+    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], CK::A51 * a1[c]))), v[c]);
+  }
+  ring_acc<N, 0>(xs, m, b, base, a5, d2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], CK::A61 * v[c])))),
+                x[c]);
+    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], CK::A61 * a1[c])))),
+                v[c]);
+  }
+  ring_acc<N, 0>(xs, m, b, base, a6, d2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], CK::B1 * v[c]))), x[c]);
+    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], CK::B1 * a1[c]))), v[c]);
+    if (E) {
+      ex[c] = h * fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], CK::E1 * v[c]))));
+      ev[c] = h * fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], CK::E1 * a1[c]))));
+    }
+  }
+}
+
+// One work unit = one warp's G = 32/N systems of a bin, integrated for the whole call.
+// ADAPT = false: fixed steps with the step-count rule of the fixed-step integrators.
+// ADAPT = true: the caller's dt is the first trial step; trials are accepted when the
+// scaled error max_b max(|ex_b|/X, |ev_b|/V) (X, V the largest body position and velocity
+// at the step's start) is at most P.rk_eps; the next trial is h * clamp(0.9 err^(-1/5)).
+template <int N, bool ADAPT>
+__device__ __forceinline__ void bpl_rkck_body(const BinView &B, const StepParams &P, int unit) {
+  using R = ARing<N>;
+  constexpr int G = 32 / N;
+  constexpr int RT = R::RTA;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {  // spare lanes mirror group 0 so every shuffle stays well defined
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int s0 = unit * G;
+  int s = s0 + g;
+  const bool sys_ok = lane_ok && s < B.S;
+  if (s >= B.S) s = s0;
+  const int SP = B.S_pad;
+
+  double x[3], v[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x[c] = B.x[(size_t)(c * N + b) * SP + s];
+    v[c] = B.v[(size_t)(c * N + b) * SP + s];
+  }
+  const double m = B.m[(size_t)b * SP + s];
+  const double t0 = B.t[s];
+  const int st0 = B.status[s];
+  const double m0 = shfl(m, base);
+  const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
+
+  // fixed steps: the launch plan; adaptive: end time and direction
+  LaunchPlan plan;
+  double te, dir = 1.0;
+  bool alive;
+  int nmax;
+  if (!ADAPT) {
+    plan = launch_plan(B, P, s, t0, runnable);
+    te = plan.t_end;
+    alive = runnable && plan.N > 0;
+    nmax = __reduce_max_sync(FULL, plan.N);
+  } else {
+    te = B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
+    dir = P.dt > 0 ? 1.0 : -1.0;
+    alive = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
+    nmax = P.max_steps > 0 ? P.max_steps : kRkckTrialCap;
+  }
+  if (!__any_sync(FULL, alive)) {
+    if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
+    return;
+  }
+
+  double kc[RT];
+#pragma unroll
+  for (int r = 1; r <= RT; r++) {
+    int p = b + r;
+    if (p >= N) p -= N;
+    double mp = shfl(m, base + p);
+    kc[r - 1] = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+  }
+  double a1[3], d2[RT];
+  ring_acc<N, 0>(x, m, b, base, a1, d2);
+
+  const bool ran = alive;
+  double t = t0;
+  double h = fabs(P.dt);
+  int steps = 0, trials = 0, code = 0;
+  bool reached = false;
+  for (int k = 1; k <= nmax; k++) {
+    if (!__any_sync(FULL, alive)) break;
+    // this trial's step (group-uniform)
+    double hs;
+    bool last;
+    if (!ADAPT) {
+      last = k == plan.N;
+      hs = (last && !plan.exact) ? plan.h_last : P.dt;
+    } else {
+      const double rem = (te - t) * dir;
+      last = h >= rem;
+      hs = (last ? rem : h) * dir;
+    }
+    double x5[3], v5[3], ex[3], ev[3];
+    rkck_stages<N, ADAPT>(x, v, a1, m, b, base, hs, x5, v5, ex, ev);
+    bool accept = alive;
+    double err = 0.0;
+    bool bad = false;
+    if (ADAPT) {
+      const double X2 = grp_max<N>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2], b, base);
+      const double V2 = grp_max<N>(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], b, base);
+      const double px = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
+      const double pv = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
+      const double rq = grp_max<N>(fmax(px / X2, pv / V2), b, base);
+      err = sqrt(rq) / P.rk_eps;
+      bad = nonfinite(err);
+      accept = alive && !bad && err <= 1.0;
+      if (alive) trials++;
+    }
+    // next first stage (and the monitor's distances) at the accepted state; a rejected
+    // group re-evaluates its unchanged state
+    double xn[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) xn[c] = accept ? x5[c] : x[c];
+    double an[3];
+    ring_acc<N, 0>(xn, m, b, base, an, d2);
+    if (accept) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[c] = x5[c];
+        v[c] = v5[c];
+        a1[c] = an[c];
+      }
+      steps++;
+      if (!ADAPT) t = step_time(plan, k, t0, P.dt);
+      else t = last ? te : t + hs;
+    }
+    // monitor on the accepted state
+    const double dq0 = x[0] - shfl(x[0], base), dq1 = x[1] - shfl(x[1], base), dq2 = x[2] - shfl(x[2], base);
+    const double q2 = dq0 * dq0 + dq1 * dq1 + dq2 * dq2;
+    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
+                    nonfinite(v[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+#pragma unroll
+    for (int r = 1; r <= RT; r++) {
+      int p = b + r;
+      if (p >= N) p -= N;
+      double q2p = shfl(q2, base + p);
+      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+    }
+    const unsigned gm = ((1u << N) - 1u) << base;
+    const unsigned bnf = __ballot_sync(FULL, (accept && nf) || (alive && bad)) & gm;
+    const unsigned bej = __ballot_sync(FULL, accept && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, accept && ce) & gm;
+    const int c2 = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (alive && c2) {
+      code = c2;
+      alive = false;
+    } else if (accept && last) {
+      reached = true;
+      alive = false;
+    }
+    if (P.log_interval > 0) {
+      const bool need = accept && !c2 && (steps % P.log_interval) == 0;
+      if (__any_sync(FULL, need)) {
+        double e4[4];
+        ring_energy<N>(x, v, m, b, base, e4);
+        if (need && b == 0 && sys_ok) write_log(P, B.gidx[s], t, e4);
+      }
+    }
+    if (ADAPT && alive) {
+      // step control (Hairer, Norsett & Wanner, Sec. II.4): safety 0.9, ratio in [0.2, 5]
+      double f;
+      if (err <= 1e-30) f = 5.0;
+      else if (err >= 1e30) f = 0.2;
+      else f = 0.9 * inv_fifth_root(err);
+      h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
+      if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) {  // step-size underflow
+        code = SWARM_SYS_NONFINITE;
+        alive = false;
+      }
+    }
+  }
+  if (sys_ok && ran) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      B.x[(size_t)(c * N + b) * SP + s] = x[c];
+      B.v[(size_t)(c * N + b) * SP + s] = v[c];
+    }
+    if (b == 0) {
+      B.t[s] = t;
+      if (ADAPT) B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+      else B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+    }
+  } else if (runnable && b == 0) {
+    B.status[s] = SWARM_SYS_DONE;  // already at its end time
+  }
+  if (P.counters && sys_ok && b == 0 && ran) {
+    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+    const unsigned long long tr = ADAPT ? (unsigned long long)trials : (unsigned long long)steps;
+    if (steps > 0) atomicAdd(&P.counters[0], (unsigned long long)steps);
+    atomicAdd(&P.counters[1], NP * (1ull + 6ull * tr));
+  }
+}
+
+// Persistent kernel for one bin: warps pull unit indices from a counter.
+template <int N, bool ADAPT>
+__global__ void __launch_bounds__(128, 2) rkck_uniform_kernel(BinView B, int nunits, StepParams P) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(P.work_next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nunits) break;
+    bpl_rkck_body<N, ADAPT>(B, P, w);
+  }
+}
+
+template <int N, bool ADAPT>
+cudaError_t launch_rkck_uniform_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
+                                  int *blocks) {
+  if (blocks) cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, rkck_uniform_kernel<N, ADAPT>, 128, 0);
+  if (grid <= 0) return cudaSuccess;
+  rkck_uniform_kernel<N, ADAPT><<<grid, 128, 0, st>>>(B, nunits, P);
+  return cudaGetLastError();
+}
+
+}  // namespace swarm

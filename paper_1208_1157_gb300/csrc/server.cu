@@ -252,7 +252,7 @@ extern "C" int swarm_server_create(const swarm_server_config *cfg, void *cuda_st
   auto sv = std::make_unique<swarm_server>();
   sv->cfg = *cfg;
   sv->stream = (cudaStream_t)cuda_stream;
-  sv->stage_doubles = (size_t)4096 * SWARM_MAX_N * 7 + 4096 * 2;
+  sv->stage_doubles = (size_t)4096 * SWARM_RING_MAX_N * 7 + 4096 * 2;
   SCK(cudaMalloc(&sv->d_stage, sizeof(double) * sv->stage_doubles));
   SCK(cudaMalloc(&sv->d_slots, sizeof(int) * 4096));
   SCK(cudaMalloc(&sv->d_counters, sizeof(unsigned long long) * 4));
@@ -285,7 +285,7 @@ extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_bo
                                    int64_t *id) {
   if (!sv || !mass || !pos || !vel || !id) return sfail(SWARM_EINVAL, "NULL argument");
   if (n_sys < 1 || n_sys > 4096) return sfail(SWARM_EINVAL, "a request holds 1..4096 systems");
-  if (n_body < SWARM_MIN_N || n_body > SWARM_MAX_N) return sfail(SWARM_EINVAL, "n_body must be in 2..15");
+  if (n_body < SWARM_MIN_N || n_body > SWARM_RING_MAX_N) return sfail(SWARM_EINVAL, "n_body must be in 2..15");
   if (integrator < SWARM_HERMITE4 || integrator > SWARM_MVS_JACOBI) return sfail(SWARM_EINVAL, "unknown integrator");
   if (!std::isfinite(t0) || !std::isfinite(t_end)) return sfail(SWARM_EINVAL, "t0 and t_end must be finite");
   if (n_sys > ((sv->cfg.slots_per_pool + 31) / 32 * 32)) return sfail(SWARM_EINVAL, "request larger than a slot pool");

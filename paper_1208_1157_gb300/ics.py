@@ -10,7 +10,7 @@ Units follow Sec. 2.1 of the paper (Eq. 1 with G = 1): lengths in AU, masses in
 solar masses, one year = 2*pi time units.  Body 0 of every system is the star.
 
 Ensemble layout returned by every generator (a dict):
-  n_body  int32  [S]       bodies per system (3..15)
+  n_body  int32  [S]       bodies per system (2..32)
   mass    float64[B]       B = sum(n_body), systems back to back, star first
   pos     float64[B, 3]    barycentric positions
   vel     float64[B, 3]    barycentric velocities
@@ -157,22 +157,25 @@ def three_body(n_sys: int, seed: int) -> dict:
     return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
 
 
-def _hill_spaced(n_body, seed, idx, e_max, base_k):
-    """a_1 = 1; a_{j+1} = a_j (1 + K h/2)/(1 - K h/2), h = ((m_j + m_{j+1})/3)^(1/3), K ~ U(3, 8)."""
+def _hill_spaced(n_body, seed, idx, e_max, base_k, m_lo=1e-5, m_hi=1e-3, stride=20):
+    """a_1 = 1; a_{j+1} = a_j (1 + K h/2)/(1 - K h/2), h = ((m_j + m_{j+1})/3)^(1/3), K ~ U(3, 8);
+    masses log-U(m_lo, m_hi).  Draw k of planet j: mass base_k + j, e base_k + stride + j,
+    K base_k + 2 stride + j, angles from base_k + 3 stride (stride > planets per system)."""
     S = len(n_body)
     P = int(n_body.max()) - 1
+    assert P < stride
     mp = np.zeros((S, P))
     a = np.zeros((S, P))
     e = np.zeros((S, P))
     for j in range(P):
-        mp[:, j] = _log_uniform(uniform(seed, idx, base_k + j), 1e-5, 1e-3)
-        e[:, j] = e_max * uniform(seed, idx, base_k + 20 + j)
+        mp[:, j] = _log_uniform(uniform(seed, idx, base_k + j), m_lo, m_hi)
+        e[:, j] = e_max * uniform(seed, idx, base_k + stride + j)
     a[:, 0] = 1.0
     for j in range(1, P):
-        K = 3.0 + 5.0 * uniform(seed, idx, base_k + 40 + j)
+        K = 3.0 + 5.0 * uniform(seed, idx, base_k + 2 * stride + j)
         h = np.cbrt((mp[:, j - 1] + mp[:, j]) / 3.0)
         a[:, j] = a[:, j - 1] * (1.0 + 0.5 * K * h) / (1.0 - 0.5 * K * h)
-    inc, node, peri, E = _angles(seed, idx, base_k + 60, P)
+    inc, node, peri, E = _angles(seed, idx, base_k + 3 * stride, P)
     return mp, a, e, inc, node, peri, E
 
 
@@ -182,6 +185,16 @@ def ragged(n_sys: int, seed: int, n_min: int = 3, n_max: int = 15) -> dict:
     idx = np.arange(n_sys)
     n_body = (n_min + np.floor((n_max - n_min + 1) * uniform(seed, idx, 0))).astype(np.int32)
     mp, a, e, inc, node, peri, E = _hill_spaced(n_body, seed, idx, 0.1, 1)
+    return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
+
+
+def ragged_wide(n_sys: int, seed: int, n_min: int = 16, n_max: int = 32) -> dict:
+    """Larger systems: n ~ U{n_min..n_max} (up to 31 planets), masses log-U(1e-7, 1e-5)
+    (Mars to Neptune mass in solar units), Hill spacing as in `ragged` (K ~ U(3, 8)),
+    e ~ U(0, 0.1); the outermost orbit stays within ~15 AU."""
+    idx = np.arange(n_sys)
+    n_body = (n_min + np.floor((n_max - n_min + 1) * uniform(seed, idx, 0))).astype(np.int32)
+    mp, a, e, inc, node, peri, E = _hill_spaced(n_body, seed, idx, 0.1, 1, m_lo=1e-7, m_hi=1e-5, stride=40)
     return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
 
 

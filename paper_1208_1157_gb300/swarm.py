@@ -16,14 +16,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswarm_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
-HERMITE4, MVS_DH, MVS_JACOBI, HERMITE4_ADAPTIVE = 1, 2, 3, 4
+HERMITE4, MVS_DH, MVS_JACOBI, HERMITE4_ADAPTIVE, RKCK, RKCK_ADAPTIVE = 1, 2, 3, 4, 5, 6
 ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE = range(6)
 MAP_AUTO, MAP_SYSTEM_PER_LANE, MAP_BODY_PER_LANE, MAP_PLAIN_PER_STEP = range(4)
 OPT_MAPPING, OPT_N_CORR, OPT_LOG_INTERVAL, OPT_LOG_CAPACITY, OPT_STEPS_PER_LAUNCH, OPT_SINGLE_LAUNCH, OPT_CTAS_PER_SM, OPT_CORRECTOR = range(1, 9)
 
 # every symbol include/swarm.h declares (checked by the ABI test)
 EXPORTS = (
-    "swarm_create_ensemble", "swarm_set_stop", "swarm_set_option", "swarm_integrate", "swarm_integrate_async",
+    "swarm_create_ensemble", "swarm_set_stop", "swarm_set_option", "swarm_set_tolerance", "swarm_query_rv",
+    "swarm_observe_rv", "swarm_integrate", "swarm_integrate_async",
     "swarm_synchronize", "swarm_set_state", "swarm_query_state", "swarm_query_state_dev", "swarm_query_diagnostics",
     "swarm_query_log", "swarm_query_stats", "swarm_ensemble_size", "swarm_destroy_ensemble", "swarm_tuner_choice",
     "swarm_tuner_load", "swarm_tuner_save", "swarm_fp64_peak", "swarm_last_error", "swarm_version",
@@ -61,6 +62,9 @@ def lib():
             L.swarm_create_ensemble.argtypes = [C.c_int32, _ip, _dp, _dp, _dp, C.c_double, _vp, C.POINTER(_vp)]
             L.swarm_set_stop.argtypes = [_vp, C.c_double, C.c_double]
             L.swarm_set_option.argtypes = [_vp, C.c_int, C.c_int64]
+            L.swarm_set_tolerance.argtypes = [_vp, C.c_double]
+            L.swarm_query_rv.argtypes = [_vp, _dp, _dp]
+            L.swarm_observe_rv.argtypes = [_vp, _dp, C.c_int32, C.c_int, C.c_double, _dp, _dp]
             L.swarm_integrate.argtypes = [_vp, C.c_double, C.c_int, C.c_double]
             L.swarm_integrate_async.argtypes = [_vp, C.c_double, C.c_int, C.c_double]
             L.swarm_synchronize.argtypes = [_vp]
@@ -139,6 +143,9 @@ class Ensemble:
     def set_stop(self, ce_factor=0.0, eject_radius=0.0):
         _check(lib().swarm_set_stop(self._h, float(ce_factor), float(eject_radius)))
 
+    def set_tolerance(self, eps):
+        _check(lib().swarm_set_tolerance(self._h, float(eps)))
+
     def set_option(self, opt, value):
         _check(lib().swarm_set_option(self._h, int(opt), int(value)))
 
@@ -189,6 +196,21 @@ class Ensemble:
         n = C.c_int32()
         _check(lib().swarm_query_log(self._h, int(sys_index), _d(rec), int(cap), C.byref(n)))
         return rec[: n.value].copy()
+
+    def rv(self, los=(0.0, 0.0, 1.0)):
+        """Radial velocity v_0 . los of every system's central body at the current state."""
+        los = np.ascontiguousarray(los, dtype=np.float64)
+        out = np.empty(self.n_sys)
+        _check(lib().swarm_query_rv(self._h, _d(los), _d(out)))
+        return out
+
+    def observe_rv(self, t_obs, integrator, dt, los=(0.0, 0.0, 1.0)):
+        """Integrate through the observation times; radial velocities [n_obs][n_sys]."""
+        t_obs = np.ascontiguousarray(t_obs, dtype=np.float64)
+        los = np.ascontiguousarray(los, dtype=np.float64)
+        out = np.empty((len(t_obs), self.n_sys))
+        _check(lib().swarm_observe_rv(self._h, _d(t_obs), len(t_obs), int(integrator), float(dt), _d(los), _d(out)))
+        return out
 
     def stats(self):
         s = Stats()

@@ -20,13 +20,15 @@ U = 2.0 ** -53  # unit round-off
 
 
 def run_gpu(ens, t_end, integrator, dt, mapping=0, ce=0.0, ej=0.0, n_corr=2, log_interval=0, log_cap=0,
-            time=None, status=None, single_launch=1):
+            time=None, status=None, single_launch=1, rk_eps=1e-12, steps_per_launch=0):
     from paper_1208_1157_gb300 import swarm as S
 
     with S.Ensemble(ens) as e:
         e.set_option(S.OPT_MAPPING, mapping)
         e.set_option(S.OPT_N_CORR, n_corr)
         e.set_option(S.OPT_SINGLE_LAUNCH, single_launch)
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, steps_per_launch)
+        e.set_tolerance(rk_eps)
         if log_cap:
             e.set_option(S.OPT_LOG_CAPACITY, log_cap)
             e.set_option(S.OPT_LOG_INTERVAL, log_interval)
@@ -43,9 +45,9 @@ def run_gpu(ens, t_end, integrator, dt, mapping=0, ce=0.0, ej=0.0, n_corr=2, log
 
 
 def run_oracle(ens, t_end, integrator, dt, ce=0.0, ej=0.0, n_corr=2, log_interval=0, log_cap=0, time=None,
-               status=None):
+               status=None, rk_eps=1e-12):
     return O.integrate(ens, t_end, dt, integrator, n_corr=n_corr, ce_factor=ce, eject_radius=ej,
-                       log_interval=log_interval, log_cap=log_cap, time=time, status=status)
+                       log_interval=log_interval, log_cap=log_cap, time=time, status=status, rk_eps=rk_eps)
 
 
 def per_system_errors(ens, a, b):
@@ -81,22 +83,40 @@ def oracle_sensitivity(ens, t_end, integrator, dt, **kw):
     return np.maximum(ex, ev)
 
 
-def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000):
+def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, stop_time_rtol=None):
     """Statuses and times equal; positions/velocities within tol (or, for systems whose
     measured round-off sensitivity `sens` exceeds tol/100, within COND_FACTOR * sens);
     the GPU's relative energy error within 2x the oracle's, or below the round-off bound
-    steps * u when the oracle's own error is at that level."""
+    steps * u when the oracle's own error is at that level.
+
+    stop_time_rtol: for an integrator whose step sizes come from an error estimate (the
+    adaptive Runge-Kutta step), the estimate is a short sum of large terms that cancel, so
+    its rounding fixes each step size only to ~1e-9 relative: a system that stops on the
+    way then stops at a time that may differ by that much.  Such systems get this time
+    tolerance, and their states the distance covered in the time difference."""
     assert np.array_equal(g["status"], o["status"]), (
         f"status mismatch at systems {np.nonzero(g['status'] != o['status'])[0][:10]}: "
         f"gpu {g['status'][g['status'] != o['status']][:10]} oracle {o['status'][g['status'] != o['status']][:10]}")
-    np.testing.assert_allclose(g["time"], o["time"], rtol=1e-13, atol=1e-13)
     ex, ev = per_system_errors(ens, g, o)
     bound = np.full(len(ex), tol)
+    tbound = np.full(len(ex), 1e-13)
     if sens is not None:
         ill = sens > tol / 100
         # the strict bar must still be exercised on most of the ensemble
         assert ill.mean() <= 0.5, f"{ill.sum()} of {len(ill)} systems ill-conditioned"
         bound = np.where(ill, np.maximum(tol, COND_FACTOR * sens), tol)
+        # an adaptive integrator's stop time follows the trajectory: same bound there
+        tbound = np.where(ill, np.maximum(1e-13, COND_FACTOR * sens), 1e-13)
+    dt_rel = np.abs(g["time"] - o["time"]) / np.maximum(np.abs(o["time"]), 1.0)
+    if stop_time_rtol is not None:
+        stopped = o["status"] >= 2
+        tbound = np.where(stopped, np.maximum(tbound, stop_time_rtol), tbound)
+        # distance covered in the time difference, relative to the system's size
+        offs = np.concatenate([[0], np.cumsum(ens["n_body"])])
+        rate = np.array([np.abs(o["vel"][offs[k]:offs[k + 1]]).max() / np.abs(o["pos"][offs[k]:offs[k + 1]]).max()
+                         for k in range(len(offs) - 1)])  # ~ orbital frequency: |dx|/|x|, |dv|/|v| per unit time
+        bound = np.where(stopped, bound + 10.0 * np.abs(g["time"] - o["time"]) * rate, bound)
+    assert np.all(dt_rel <= tbound), f"time mismatch at {np.nonzero(dt_rel > tbound)[0][:10]}: {dt_rel[dt_rel > tbound][:5]}"
     r = np.maximum(ex, ev) / bound
     worst = int(np.argmax(r))
     sw = "n/a" if sens is None else f"{sens[worst]:.3e}"

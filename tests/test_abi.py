@@ -62,7 +62,7 @@ def test_create_rejects_bad_input_on_host(S, case):
     if case == "n_too_small":
         ens = {"n_body": np.array([1]), "mass": np.array([1.0]), "pos": np.zeros((1, 3)), "vel": np.zeros((1, 3))}
     elif case == "n_too_large":
-        ens = {"n_body": np.array([16]), "mass": np.ones(16), "pos": np.arange(48.0).reshape(16, 3), "vel": np.zeros((16, 3))}
+        ens = {"n_body": np.array([33]), "mass": np.ones(33), "pos": np.arange(99.0).reshape(33, 3), "vel": np.zeros((33, 3))}
     elif case == "nan_pos":
         ens["pos"][4, 1] = np.nan
     elif case == "zero_mass":

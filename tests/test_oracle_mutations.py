@@ -38,6 +38,8 @@ MUTANTS = {
     "rkck_propagate_b4": ("sx += RK_B5[s] * kx[s][q];", "sx += RK_B4[s] * kx[s][q];"),
     "rkck_stage_velocity": ("for (int q = 0; q < d; q++) kx[s][q] = vs[q];", "for (int q = 0; q < d; q++) kx[s][q] = v[q];"),
     "rkck_accept_loose": ("if (err <= 1.0) {", "if (err <= 100.0) {"),
+    "rv_wrong_body": ("rv[k] = v[0] * los[0] + v[1] * los[1] + v[2] * los[2];",
+                      "rv[k] = v[3] * los[0] + v[4] * los[1] + v[5] * los[2];"),
     "rkck_error_weights": ("tx += (RK_B5[s] - RK_B4[s]) * kx[s][q];", "tx += (RK_B5[s] - RK_B4[s]) * kv[s][q];"),
 }
 

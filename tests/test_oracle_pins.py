@@ -664,3 +664,25 @@ def test_rkck_adaptive_never_accepts_a_step_above_tolerance():
     assert out["time"][0] == h and steps >= 2
     r_ref, _ = cf.elliptic_at(mu, 1.0, e, 0.0, h)
     assert np.linalg.norm(out["pos"][1] - out["pos"][0] - r_ref) <= 3.0 * steps * eps
+
+
+# ----------------------------------------------------------------- radial-velocity observable
+def test_star_radial_velocity_of_a_circular_orbit():
+    # circular two-body orbit seen at inclination i along z: the star moves on a circle of
+    # speed m1/(m0+m1) sqrt(mu/a), half a turn out of phase with the planet, so its
+    # z-velocity is -(m1/mu) sqrt(mu/a) sin(i) cos(n t + phase) for an orbit in the tilted
+    # plane; the sign convention is rv = v_0 . los with los pointing away from the observer
+    m0, m1, a, inc = 1.0, 1e-3, 1.3, 0.7
+    mu = m0 + m1
+    nmot = math.sqrt(mu / a ** 3)
+    r = np.array([a, 0.0, 0.0])
+    u = math.sqrt(mu / a) * np.array([0.0, math.cos(inc), math.sin(inc)])
+    s = {"n_body": np.array([2], np.int32), "mass": np.array([m0, m1]),
+         "pos": np.array([-m1 / mu * r, m0 / mu * r]), "vel": np.array([-m1 / mu * u, m0 / mu * u])}
+    t_obs = np.linspace(0.1, 10.0, 9)
+    out = O.observe_rv(s, t_obs, 1e-3, O.HERMITE, los=(0.0, 0.0, 1.0))
+    want = -(m1 / mu) * math.sqrt(mu / a) * math.sin(inc) * np.cos(nmot * t_obs)
+    assert np.abs(out["rv"][:, 0] - want).max() < 1e-12
+    # the line of sight reverses the sign
+    back = O.observe_rv(s, t_obs, 1e-3, O.HERMITE, los=(0.0, 0.0, -1.0))
+    assert np.array_equal(back["rv"], -out["rv"])
