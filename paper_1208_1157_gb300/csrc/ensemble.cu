@@ -93,6 +93,10 @@ struct swarm_ensemble {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // chunked launches (SWARM_OPT_STEPS_PER_LAUNCH): captured once, replayed
   cudaStream_t cap_stream = nullptr;
+  // concurrent single-bin launches: side streams forked from and joined to the main one
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork_ev = nullptr;
   double *d_tend = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
@@ -201,6 +205,24 @@ static void free_all(swarm_ensemble *e) {
   if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->d_tend) cudaFree(e->d_tend);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  for (auto st : e->side) cudaStreamDestroy(st);
+  for (auto ev : e->side_done) cudaEventDestroy(ev);
+  if (e->fork_ev) cudaEventDestroy(e->fork_ev);
+}
+
+constexpr int kSideStreams = 8;
+static int ensure_side(swarm_ensemble *e) {
+  if (!e->side.empty()) return SWARM_OK;
+  CK(cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming));
+  for (int i = 0; i < kSideStreams; i++) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    e->side.push_back(st);
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    e->side_done.push_back(ev);
+  }
+  return SWARM_OK;
 }
 
 static int upload_state(swarm_ensemble *e, const double *pos, const double *vel, const double *mass,
@@ -624,28 +646,43 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     if (!ctas || ctas > maxb) ctas = maxb;
     grid = std::max(1, std::min(sms * ctas, (e->nwork + 3) / 4));
   }
+  // With more than one launch per round, the single-bin launches run on side streams
+  // forked from the main stream (heaviest bin first), so that one launch's tail overlaps
+  // the next launch's work; all of them join the main stream before the round ends.
+  const int nconc = (int)uni.size() + (per_bin ? 0 : 1);
+  if (nconc > 1 && (rc = ensure_side(e))) return rc;
   auto enqueue = [&](cudaStream_t cs, const StepParams &Q) -> int {
-    // single-bin launches (every bin, or only the wide bins next to the shared launch),
-    // each with its own work counter after the shared launch's
-    for (size_t i = 0; i < uni.size(); i++) {
-      StepParams Qi = Q;
-      Qi.work_next = e->d_work_next + 1 + i;
-      CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), cs));
-      if (uni[i].mapping == kMapWide)
-        CK(launch_hermite_wide(uni[i].view, Qi, uni[i].grid, cs, nullptr));
-      else if (hermite_family(integrator))
-        CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr,
-                                  uni[i].variant));
-      else if (rkck_family(integrator))
-        CK(launch_rkck_uniform(uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs, nullptr));
-      else
-        CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, cs,
-                              nullptr));
+    const int K = nconc > 1 ? std::min((int)uni.size(), kSideStreams) : 0;
+    if (K) {
+      CK(cudaEventRecord(e->fork_ev, cs));
+      for (int j = 0; j < K; j++) CK(cudaStreamWaitEvent(e->side[j], e->fork_ev, 0));
     }
-    if (!per_bin) {
+    if (!per_bin) {  // the shared launch stays on the main stream
       CK(cudaMemsetAsync(e->d_work_next, 0, sizeof(int), cs));
       if (hermite_family(integrator)) CK(launch_hermite_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
       else CK(launch_mvs_persistent(e->d_bins, e->d_work, e->nwork, Q, grid, cs));
+    }
+    // single-bin launches (every bin, or only the wide bins next to the shared launch),
+    // each with its own work counter after the shared launch's
+    for (size_t i = 0; i < uni.size(); i++) {
+      cudaStream_t si = K ? e->side[i % K] : cs;
+      StepParams Qi = Q;
+      Qi.work_next = e->d_work_next + 1 + i;
+      CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), si));
+      if (uni[i].mapping == kMapWide)
+        CK(launch_hermite_wide(uni[i].view, Qi, uni[i].grid, si, nullptr));
+      else if (hermite_family(integrator))
+        CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, si, nullptr,
+                                  uni[i].variant));
+      else if (rkck_family(integrator))
+        CK(launch_rkck_uniform(uni[i].view, uni[i].nunits, Qi, uni[i].grid, si, nullptr));
+      else
+        CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, si,
+                              nullptr));
+    }
+    for (int j = 0; j < K; j++) {
+      CK(cudaEventRecord(e->side_done[j], e->side[j]));
+      CK(cudaStreamWaitEvent(cs, e->side_done[j], 0));
     }
     return SWARM_OK;
   };

@@ -523,17 +523,221 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
   bpl_mvs_body<N, JAC>(B, P, unit);
 }
 
-// Persistent kernel for one bin (see hermite_uniform_kernel).
+// ---------------------------------------------------------------- group refill
+// The same steps with work handed out per system instead of per warp: each of the warp's
+// G groups takes the next system of the bin (a per-bin counter) whenever its own system
+// has stopped or reached its end time, so a warp does not carry finished groups along
+// until its last system is done (in compact ensembles most systems stop early).  A refill
+// costs the warp one round (the new systems' coordinate maps and first force
+// evaluation) during which the other groups wait.  Per system the arithmetic is that of
+// bpl_mvs_body, step for step.
+template <int N, bool JAC>
+__device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParams &P) {
+  constexpr int G = 32 / N;
+  constexpr int MR = JAC ? N : N - 1;
+  constexpr int RTA = ARing<MR>::RTA;
+  constexpr int RT = ARing<MR>::RT;
+  constexpr unsigned long long NP = JAC ? (unsigned long long)N * (N - 1) / 2 : (unsigned long long)(N - 1) * (N - 2) / 2;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {  // spare lanes mirror group 0 (same broadcasts, same state)
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int SP = B.S_pad;
+  const unsigned gm = ((1u << N) - 1u) << base;
+
+  // the group's current system and its constants (group-uniform)
+  int s = 0;
+  bool has = false, exhausted = false;
+  double m = 1.0, m0 = 1.0, Minv = 1.0, eta_prev_inv = 0.0, w = 1.0, mu = 1.0, m0inv = 1.0;
+  KepConst K = kep_const(1.0);
+  double kc[RTA];
+  LaunchPlan plan;
+  plan.N = 0;
+  plan.full = 1;
+  plan.exact = 1;
+  plan.h_last = P.dt;
+  plan.t_end = P.t_end;
+  double t0 = 0.0;
+  int kg = 0;
+  double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
+  double chi = 0.0;
+  bool have_chi = false;
+  unsigned long long kep_iters = 0;
+#pragma unroll
+  for (int r = 0; r < RTA; r++) kc[r] = 0.0;
+
+  for (;;) {
+    // ---- refill: groups without a system take the bin's next one
+    const bool need = !has && !exhausted;
+    if (__any_sync(FULL, need)) {
+      int sn = 0;
+      if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
+      sn = __shfl_sync(FULL, sn, base);
+      const bool take = need && sn < B.S;
+      if (need && sn >= B.S) exhausted = true;
+      const int sl = take ? sn : s;  // a valid row for every lane's loads
+      double xn[3], vn[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        xn[c] = B.x[(size_t)(c * N + b) * SP + sl];
+        vn[c] = B.v[(size_t)(c * N + b) * SP + sl];
+      }
+      // constants: recomputed from the same masses for groups that keep their system
+      const double mn = take ? B.m[(size_t)b * SP + sl] : m;
+      m = mn;
+      m0 = shfl(m, base);
+      const double Mtot = grp_sum<N>(m, b, base);
+      Minv = 1.0 / Mtot;
+      const double eta = grp_scan_excl<N>(m, b) + m;
+      const double eta_prev = eta - m;
+      eta_prev_inv = b == 0 ? 0.0 : 1.0 / eta_prev;
+      w = m / eta;
+      mu = JAC ? (b == 0 ? m0 : m0 * eta * eta_prev_inv) : m0;
+      K = kep_const(mu);
+      m0inv = 1.0 / m0;
+      {
+        const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
+#pragma unroll
+        for (int r = 1; r <= RTA; r++) {
+          int p = jm + r;
+          if (p >= MR) p -= MR;
+          const int pl = JAC ? p : p + 1;
+          double mp = shfl(m, base + (JAC ? 0 : 1) + p);
+          kc[r - 1] = (b != 0 && pl != 0 && r <= RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+        }
+      }
+      double qn[3], un[3];
+      if (JAC) to_jacobi<N>(xn, vn, m, Minv, eta_prev_inv, b, base, qn, un);
+      else to_dh<N>(xn, vn, m, Minv, b, base, qn, un);
+      double an[3], Qn[3], d2n[RTA];
+#pragma unroll
+      for (int r = 0; r < RTA; r++) d2n[r] = 0.0;
+      mvs_acc<N, JAC>(qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n);
+      if (take) {
+        s = sn;
+        const double tn = B.t[s];
+        const bool runnable = B.status[s] <= SWARM_SYS_DONE;
+        plan = launch_plan(B, P, s, tn, runnable);
+        t0 = tn;
+        kg = 0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          q[c] = qn[c];
+          u[c] = un[c];
+          acc[c] = an[c];
+        }
+        chi = 0.0;
+        have_chi = false;
+        has = plan.N > 0;
+        if (runnable && plan.N == 0 && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
+      }
+      continue;
+    }
+    if (!__any_sync(FULL, has)) break;
+
+    // ---- one step for every group holding a system
+    const bool active = has;
+    if (active) kg++;
+    const double h = (active && kg == plan.N && !plan.exact) ? plan.h_last : P.dt;
+    const double hh = 0.5 * h;
+    if (!JAC) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+        if (b == 0) q[c] = fma(h, u[c], q[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
+    int its = 0;
+    const bool ok = kepler_drift(active && b != 0, K, q, u, h, chi, have_chi, its);
+    if (active) have_chi = true;
+    kep_iters += its;
+    double Q[3], d2[RTA];
+#pragma unroll
+    for (int r = 0; r < RTA; r++) d2[r] = 0.0;
+    mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
+    if (!JAC) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        Q[c] = q[c];
+      }
+    }
+    // monitor on the heliocentric positions at the end of the step
+    const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    const bool nf = nonfinite(q[0]) | nonfinite(q[1]) | nonfinite(q[2]) | nonfinite(u[0]) | nonfinite(u[1]) |
+                    nonfinite(u[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+    {
+      const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
+#pragma unroll
+      for (int r = 1; r <= RTA; r++) {
+        int p = jm + r;
+        if (p >= MR) p -= MR;
+        double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
+        if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      }
+    }
+    const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
+    const unsigned bkn = __ballot_sync(FULL, active && !ok) & gm;
+    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+    const int code = bkn ? SWARM_SYS_KEPLER_NOCONV
+                         : bnf ? SWARM_SYS_NONFINITE
+                               : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    const bool finish = active && (code != 0 || kg == plan.N);
+    const bool want_log = active && !code && P.log_interval > 0 && (kg % P.log_interval) == 0;
+    if (__any_sync(FULL, finish || want_log)) {
+      double xo[3], vo[3];
+      if (JAC) from_jacobi<N>(q, u, w, b, base, xo, vo);
+      else from_dh<N>(q, u, m, m0, Minv, b, base, xo, vo);
+      const double tk = step_time(plan, kg, t0, P.dt);
+      if (__any_sync(FULL, want_log)) {  // the energy sum is a warp collective
+        double e[4];
+        ring_energy<N>(xo, vo, m, b, base, e);
+        if (want_log && lane_ok && b == 0) write_log(P, B.gidx[s], tk, e);
+      }
+      if (finish && lane_ok) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          B.x[(size_t)(c * N + b) * SP + s] = xo[c];
+          B.v[(size_t)(c * N + b) * SP + s] = vo[c];
+        }
+        if (b == 0) {
+          B.t[s] = tk;
+          B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+          if (P.counters) {
+            atomicAdd(&P.counters[0], (unsigned long long)kg);
+            atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)kg));
+          }
+        }
+      }
+      if (finish) has = false;
+    }
+  }
+  if (P.counters && lane_ok && kep_iters) atomicAdd(&P.counters[2], kep_iters);
+}
+
+// Persistent kernel for one bin: every warp streams systems through its groups until the
+// bin's counter runs out (work unit = system).
 template <int N, bool JAC>
 __global__ void __launch_bounds__(128, 2) mvs_uniform_kernel(BinView B, int nunits, StepParams P) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(P.work_next, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= nunits) break;
-    bpl_mvs_body<N, JAC>(B, P, w);
-  }
+  (void)nunits;
+  bpl_mvs_stream<N, JAC>(B, P);
 }
 
 template <int N, bool JAC>
