@@ -148,6 +148,39 @@ def _oracle_chunk(args):
     return time.perf_counter() - t
 
 
+def _oracle_config_rate(name):
+    """Single-core oracle rate on a small sample of one workload (system-steps/s)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import oracle as O
+    from paper_1208_1157_gb300 import ics
+
+    if name == "c1_three_body_1024":
+        ens, integ, dt, steps = ics.three_body(1024, 1), O.HERMITE, DT, 1000
+    elif name == "c2_three_body_sample_512":
+        ens, integ, dt, steps = ics.subset(ics.three_body(512 * 64, 2), list(range(0, 512 * 64, 64))), O.HERMITE, DT, 2000
+    elif name == "c3_ragged_sample_1024":
+        ens, integ, dt, steps = ics.subset(ics.ragged(1024 * 64, 3), list(range(0, 1024 * 64, 64))), O.HERMITE, DT, 100
+    else:  # c4 compact 8-body sample, Jacobi MVS
+        ens, integ, dt, steps = ics.subset(ics.mvs_compact(256 * 64, 4), list(range(0, 256 * 64, 64))), O.MVS_JACOBI, TWO_PI / 20, 2000
+    t = time.perf_counter()
+    out = O.integrate(ens, steps * dt, dt, integ, ce_factor=3.0, eject_radius=100.0)
+    wall = time.perf_counter() - t
+    done = float(np.sum(np.round(out["time"] / dt)))
+    return name, {"system_steps_per_s": done / wall, "systems": len(ens["n_body"]), "steps_per_system": steps,
+                  "wall_s": wall}
+
+
+def oracle_config_rates():
+    """The oracle on one host core per workload (spawned before any CUDA use): C1 whole,
+    every 64th system of C2, C3 and C4."""
+    ctx = mp.get_context("spawn")
+    names = ["c1_three_body_1024", "c2_three_body_sample_512", "c3_ragged_sample_1024", "c4_mvs_jacobi_sample_256"]
+    with ctx.Pool(len(names)) as pool:
+        return dict(pool.map(_oracle_config_rate, names))
+
+
 def oracle_throughput(target_s=15.0, steps=STEPS_PER_CALL, seed=2):
     """The oracle as it stands, one process per host core (spawned before any CUDA use),
     on a sample of systems sized for about target_s seconds of wall time."""
@@ -220,7 +253,9 @@ def secondary(S, torch, stream):
 
     out = {}
 
-    def timed(ens, t_end, integ, dt, mapping=0, ce=3.0, ej=100.0, ctas=0):
+    def timed(ens, t_end, integ, dt, mapping=0, ce=3.0, ej=100.0, ctas=0, outcome=False):
+        import numpy as np
+
         with S.Ensemble(ens, stream=stream) as e:
             e.set_option(S.OPT_MAPPING, mapping)
             e.set_option(S.OPT_CTAS_PER_SM, ctas)
@@ -228,12 +263,29 @@ def secondary(S, torch, stream):
             e.integrate(min(t_end, 2 * dt), integ, dt)  # warm-up (tuner, caches)
             e.set_state(ens["pos"], ens["vel"], time=[0.0] * len(ens["n_body"]),
                         status=[0] * len(ens["n_body"]))
+            E0 = e.diagnostics()[0] if outcome else None
             e.integrate(t_end, integ, dt)
             st = e.stats()
+            if outcome:
+                E1 = e.diagnostics()[0]
+                status = e.state()["status"]
         sec = st["kernel_ms"] * 1e-3
-        return {"system_steps_per_s": st["system_steps"] / sec, "pair_interactions_per_s": st["pair_evaluations"] / sec,
-                "kernel_ms": st["kernel_ms"], "launches": st["kernel_launches"], "system_steps": st["system_steps"],
-                "kepler_iterations": st["kepler_iterations"]}
+        out = {"system_steps_per_s": st["system_steps"] / sec, "pair_interactions_per_s": st["pair_evaluations"] / sec,
+               "kernel_ms": st["kernel_ms"], "launches": st["kernel_launches"], "system_steps": st["system_steps"],
+               "kepler_iterations": st["kepler_iterations"]}
+        if outcome:
+            # stop outcomes, |dE/E| of the systems that reached t_end, Newton iterations per planet drift
+            names = ["active", "done", "close_encounter", "ejected", "kepler_noconv", "nonfinite"]
+            cnt = np.bincount(status, minlength=6)
+            dE = np.abs(E1 / E0 - 1.0)[status == 1]
+            out["status_counts"] = {names[k]: int(cnt[k]) for k in range(6)}
+            if len(dE):
+                out["energy_error_done"] = {"p50": float(np.percentile(dE, 50)), "p90": float(np.percentile(dE, 90)),
+                                            "max": float(dE.max())}
+            planets = int(np.mean(np.asarray(ens["n_body"]))) - 1
+            if st["kepler_iterations"]:
+                out["newton_iterations_per_drift"] = st["kepler_iterations"] / max(1, st["system_steps"] * planets)
+        return out
 
     c2 = ics.three_body(N_SYS, seed=2)
     out["c2_plain_one_launch_per_step_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_PLAIN_PER_STEP)
@@ -246,15 +298,15 @@ def secondary(S, torch, stream):
     out["c2_persistent_system_per_lane_3cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE,
                                                           ctas=3)
     c3 = ics.ragged(65536, seed=3)
-    out["c3_ragged_hermite_per_bin_launches_4_steps"] = timed_per_bin(S, stream, c3, 4 * DT, DT)
-    out["c3_ragged_hermite_single_launch_4_steps"] = timed(c3, 4 * DT, S.HERMITE4, DT)
+    out["c3_ragged_hermite_per_bin_launches_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT)
+    out["c3_ragged_hermite_single_launch_100_steps"] = timed(c3, 100 * DT, S.HERMITE4, DT)
     c4 = ics.mvs_compact(16384, seed=4)
-    out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
-    out["c4_mvs_dh_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20)
+    out["c4_mvs_jacobi_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, outcome=True)
+    out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)
     out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
     out["c2_rkck_fixed_500"] = timed(c2, 500 * DT, S.RKCK, DT)
     out["c2_rkck_adaptive_eps_1e-12_one_period"] = timed(c2, TWO_PI, S.RKCK_ADAPTIVE, 0.05)
-    out["c3_ragged_rkck_4_steps"] = timed(c3, 4 * DT, S.RKCK, DT)
+    out["c3_ragged_rkck_100_steps"] = timed(c3, 100 * DT, S.RKCK, DT)
     c6 = ics.ragged_wide(16384, seed=6)
     out["wide_16_to_32_bodies_hermite_20_steps"] = timed(c6, 20 * DT, S.HERMITE4, DT)
     out["serving"] = serving(S, stream)
@@ -316,6 +368,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(target_s=args.cpu_seconds)
         log(f"cpu baseline: {cpu['value']:.3e} system-steps/s on {cpu['cores']} cores")
+        if not args.no_secondary:
+            cpu["single_core_by_workload"] = oracle_config_rates()
 
     import numpy as np
     import torch

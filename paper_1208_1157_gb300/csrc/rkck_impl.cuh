@@ -295,17 +295,210 @@ __device__ __forceinline__ void bpl_rkck_body(const BinView &B, const StepParams
   }
 }
 
-// Persistent kernel for one bin: warps pull unit indices from a counter.
+// The same integration with work handed out per system: each of the warp's G groups
+// takes the bin's next system (a per-bin counter) as soon as its own one has reached its
+// end time or stopped, so groups whose systems need fewer (adaptive) steps or stop early
+// do not idle until the warp's last system is done.  A refill round loads the new
+// systems and evaluates their first stage (the other groups re-evaluate their unchanged
+// state, which gives the same values); per system the arithmetic is that of
+// bpl_rkck_body.
+template <int N, bool ADAPT>
+__device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepParams &P) {
+  using R = ARing<N>;
+  constexpr int G = 32 / N;
+  constexpr int RT = R::RTA;
+  constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {  // spare lanes mirror group 0 (same broadcasts, same state)
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int SP = B.S_pad;
+  const unsigned gm = ((1u << N) - 1u) << base;
+  const double dir = P.dt > 0 ? 1.0 : -1.0;
+  const int nmax = ADAPT ? (P.max_steps > 0 ? P.max_steps : kRkckTrialCap) : 0;
+
+  int s = 0;
+  bool has = false, exhausted = false;
+  double x[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0}, m = 1.0, a1[3], kc[RT];
+  LaunchPlan plan;
+  plan.N = 0;
+  plan.full = 1;
+  plan.exact = 1;
+  plan.h_last = P.dt;
+  plan.t_end = P.t_end;
+  double t = 0.0, t0 = 0.0, te = 0.0, h = fabs(P.dt);
+  int steps = 0, trials = 0;
+#pragma unroll
+  for (int r = 0; r < RT; r++) kc[r] = 0.0;
+
+  for (;;) {
+    // ---- refill: groups without a system take the bin's next one
+    const bool need = !has && !exhausted;
+    if (__any_sync(FULL, need)) {
+      int sn = 0;
+      if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
+      sn = __shfl_sync(FULL, sn, base);
+      const bool take = need && sn < B.S;
+      if (need && sn >= B.S) exhausted = true;
+      if (take) {
+        s = sn;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          x[c] = B.x[(size_t)(c * N + b) * SP + s];
+          v[c] = B.v[(size_t)(c * N + b) * SP + s];
+        }
+        m = B.m[(size_t)b * SP + s];
+      }
+      const double m0 = shfl(m, base);
+#pragma unroll
+      for (int r = 1; r <= RT; r++) {
+        int p = b + r;
+        if (p >= N) p -= N;
+        double mp = shfl(m, base + p);
+        const double k = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+        if (take) kc[r - 1] = k;
+      }
+      double an[3], d2[RT];
+      ring_acc<N, 0>(x, m, b, base, an, d2);
+      if (take) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) a1[c] = an[c];
+        t0 = B.t[s];
+        t = t0;
+        steps = 0;
+        trials = 0;
+        h = fabs(P.dt);
+        const bool runnable = B.status[s] <= SWARM_SYS_DONE;
+        bool go;
+        if (!ADAPT) {
+          plan = launch_plan(B, P, s, t0, runnable);
+          te = plan.t_end;
+          go = runnable && plan.N > 0;
+        } else {
+          te = B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
+          go = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
+        }
+        has = go;
+        if (runnable && !go && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
+      }
+      continue;
+    }
+    if (!__any_sync(FULL, has)) break;
+
+    // ---- one step (or trial) for every group holding a system
+    const bool alive = has;
+    double hs;
+    bool last;
+    if (!ADAPT) {
+      last = steps + 1 == plan.N;
+      hs = (last && !plan.exact) ? plan.h_last : P.dt;
+    } else {
+      const double rem = (te - t) * dir;
+      last = h >= rem;
+      hs = (last ? rem : h) * dir;
+    }
+    double x5[3], v5[3], ex[3], ev[3];
+    rkck_stages<N, ADAPT>(x, v, a1, m, b, base, hs, x5, v5, ex, ev);
+    bool accept = alive;
+    double err = 0.0;
+    bool bad = false;
+    if (ADAPT) {
+      const double X2 = grp_max<N>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2], b, base);
+      const double V2 = grp_max<N>(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], b, base);
+      const double px = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
+      const double pv = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
+      const double rq = grp_max<N>(fmax(px / X2, pv / V2), b, base);
+      err = sqrt(rq) / P.rk_eps;
+      bad = nonfinite(err);
+      accept = alive && !bad && err <= 1.0;
+      if (alive) trials++;
+    }
+    double xn[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) xn[c] = accept ? x5[c] : x[c];
+    double an[3], d2[RT];
+    ring_acc<N, 0>(xn, m, b, base, an, d2);
+    if (accept) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[c] = x5[c];
+        v[c] = v5[c];
+        a1[c] = an[c];
+      }
+      steps++;
+      if (!ADAPT) t = step_time(plan, steps, t0, P.dt);
+      else t = last ? te : t + hs;
+    }
+    const double dq0 = x[0] - shfl(x[0], base), dq1 = x[1] - shfl(x[1], base), dq2 = x[2] - shfl(x[2], base);
+    const double q2 = dq0 * dq0 + dq1 * dq1 + dq2 * dq2;
+    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
+                    nonfinite(v[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+#pragma unroll
+    for (int r = 1; r <= RT; r++) {
+      int p = b + r;
+      if (p >= N) p -= N;
+      double q2p = shfl(q2, base + p);
+      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+    }
+    const unsigned bnf = __ballot_sync(FULL, (accept && nf) || (alive && bad)) & gm;
+    const unsigned bej = __ballot_sync(FULL, accept && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, accept && ce) & gm;
+    int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (!alive) code = 0;
+    bool reached = accept && last && !code;
+    if (P.log_interval > 0) {
+      const bool need_log = accept && !code && (steps % P.log_interval) == 0;
+      if (__any_sync(FULL, need_log)) {
+        double e4[4];
+        ring_energy<N>(x, v, m, b, base, e4);
+        if (need_log && lane_ok && b == 0) write_log(P, B.gidx[s], t, e4);
+      }
+    }
+    if (ADAPT && alive && !code && !reached) {
+      double f;
+      if (err <= 1e-30) f = 5.0;
+      else if (err >= 1e30) f = 0.2;
+      else f = 0.9 * inv_fifth_root(err);
+      h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
+      if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) code = SWARM_SYS_NONFINITE;  // step-size underflow
+    }
+    const bool capped = ADAPT && alive && trials >= nmax;
+    const bool finish = alive && (code != 0 || reached || capped);
+    if (finish && lane_ok) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + b) * SP + s] = x[c];
+        B.v[(size_t)(c * N + b) * SP + s] = v[c];
+      }
+      if (b == 0) {
+        B.t[s] = t;
+        if (code) B.status[s] = code;
+        else if (ADAPT) B.status[s] = reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+        else B.status[s] = plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+        if (P.counters) {
+          const unsigned long long tr = ADAPT ? (unsigned long long)trials : (unsigned long long)steps;
+          if (steps > 0) atomicAdd(&P.counters[0], (unsigned long long)steps);
+          atomicAdd(&P.counters[1], NP * (1ull + 6ull * tr));
+        }
+      }
+    }
+    if (finish) has = false;
+  }
+}
+
+// Persistent kernel for one bin: every warp streams systems through its groups until the
+// bin's counter runs out (work unit = system).
 template <int N, bool ADAPT>
 __global__ void __launch_bounds__(128, 2) rkck_uniform_kernel(BinView B, int nunits, StepParams P) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(P.work_next, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= nunits) break;
-    bpl_rkck_body<N, ADAPT>(B, P, w);
-  }
+  (void)nunits;
+  bpl_rkck_stream<N, ADAPT>(B, P);
 }
 
 template <int N, bool ADAPT>
