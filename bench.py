@@ -299,9 +299,11 @@ def secondary(S, torch, stream):
                                                           ctas=3)
     c3 = ics.ragged(65536, seed=3)
     out["c3_ragged_hermite_per_bin_launches_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT)
-    out["c3_ragged_hermite_single_launch_100_steps"] = timed(c3, 100 * DT, S.HERMITE4, DT)
+    out["c3_ragged_hermite_single_launch_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT, single=1)
     c4 = ics.mvs_compact(16384, seed=4)
+    out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
     out["c4_mvs_jacobi_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, outcome=True)
+    out["c4_mvs_jacobi_1e5_steps_1cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=1)
     out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)
     out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
     out["c2_rkck_fixed_500"] = timed(c2, 500 * DT, S.RKCK, DT)
@@ -313,10 +315,11 @@ def secondary(S, torch, stream):
     return out
 
 
-def timed_per_bin(S, stream, ens, t_end, dt):
-    """The ragged ensemble with one single-bin launch per body count (no shared work list)."""
+def timed_per_bin(S, stream, ens, t_end, dt, single=0):
+    """The ragged ensemble with one single-bin launch per body count (single = 0, the
+    default) or one shared launch over all bins (single = 1)."""
     with S.Ensemble(ens, stream=stream) as e:
-        e.set_option(S.OPT_SINGLE_LAUNCH, 0)
+        e.set_option(S.OPT_SINGLE_LAUNCH, single)
         e.integrate(2 * dt, S.HERMITE4, dt)
         e.set_state(ens["pos"], ens["vel"], time=[0.0] * len(ens["n_body"]), status=[0] * len(ens["n_body"]))
         e.integrate(t_end, S.HERMITE4, dt)

@@ -94,8 +94,11 @@ enum swarm_option {
   SWARM_OPT_LOG_CAPACITY = 4,   /* records kept per system (ring of this size), 0..65536 */
   SWARM_OPT_STEPS_PER_LAUNCH = 5,/* 0 = whole call in one persistent launch; else launches of
                                     this many steps, replayed from a captured CUDA graph */
-  SWARM_OPT_SINGLE_LAUNCH = 6,  /* 1 (default): all n-bins share one persistent launch with a
-                                    cost-ordered work list; 0: one launch per bin */
+  SWARM_OPT_SINGLE_LAUNCH = 6,  /* 0 (default): one single-bin launch per body count (registers
+                                    sized for that n, systems handed out per group), the
+                                    launches run concurrently on forked streams; 1: the bins
+                                    with n <= 15 share one persistent launch with a cost-ordered
+                                    work list (Hermite and MVS) */
   SWARM_OPT_CTAS_PER_SM = 7,    /* persistent grid size per SM (0 = tuner/default) */
   SWARM_OPT_CORRECTOR = 8       /* Hermite corrector: 0 = time-symmetric form of Kokubo et al. 1998
                                    (default); 1 = the printed Eq. 4 read with 3/20 and the predicted

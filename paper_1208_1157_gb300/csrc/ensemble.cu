@@ -85,7 +85,7 @@ struct swarm_ensemble {
   PlainScratch plain{};
   int64_t plain_cap = 0;
   void *plain_block = nullptr;
-  int mapping = SWARM_MAP_AUTO, n_corr = 2, steps_per_launch = 0, single_launch = 1, ctas_per_sm = 0;
+  int mapping = SWARM_MAP_AUTO, n_corr = 2, steps_per_launch = 0, single_launch = 0, ctas_per_sm = 0;
   int corr_form = 0;
   double ce = 0.0, eject = 0.0;
   double rk_eps = 1e-12;  // adaptive Runge-Kutta tolerance

@@ -766,6 +766,213 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
   }
 }
 
+// Body per lane with work handed out per system: each of the warp's G groups takes the
+// bin's next system as soon as its own one reached its end time or stopped (fixed steps:
+// stops and per-system end times; adaptive steps: step counts differ from system to
+// system).  A refill round loads the new systems and evaluates their a0, j0 (the other
+// groups re-evaluate their unchanged state, which gives the same values); per system
+// the arithmetic is that of bpl_hermite_body / bpl_hermite_adaptive_body.
+template <int N, bool ADAPT>
+__device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepParams &P) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
+  using R = Ring<N>;
+  constexpr int G = R::G;
+  constexpr int RT = R::RT > 0 ? R::RT : 1;
+  constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int g = lane / N, b = lane - g * N;
+  const bool lane_ok = g < G;
+  if (!lane_ok) {  // spare lanes mirror group 0 (same broadcasts, same state)
+    g = 0;
+    b = lane - G * N;
+  }
+  const int base = g * N;
+  const int SP = B.S_pad;
+  const unsigned gm = ((1u << N) - 1u) << base;
+  const double tau = fabs(P.dt), dir = P.dt > 0 ? 1.0 : -1.0;
+  const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
+  const HCoef cdt = hcoef(P.dt);
+
+  int s = 0;
+  bool has = false, exhausted = false;
+  double x[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0}, m = 1.0, a0[3], j0[3], kc[RT];
+  LaunchPlan plan;
+  plan.N = 0;
+  plan.full = 1;
+  plan.exact = 1;
+  plan.h_last = P.dt;
+  plan.t_end = P.t_end;
+  double t = 0.0, t0 = 0.0, te = 0.0;
+  int steps = 0;
+#pragma unroll
+  for (int r = 0; r < RT; r++) kc[r] = 0.0;
+
+  for (;;) {
+    // ---- refill: groups without a system take the bin's next one
+    const bool need = !has && !exhausted;
+    if (__any_sync(FULL, need)) {
+      int sn = 0;
+      if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
+      sn = __shfl_sync(FULL, sn, base);
+      const bool take = need && sn < B.S;
+      if (need && sn >= B.S) exhausted = true;
+      if (take) {
+        s = sn;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          x[c] = B.x[(size_t)(c * N + b) * SP + s];
+          v[c] = B.v[(size_t)(c * N + b) * SP + s];
+        }
+        m = B.m[(size_t)b * SP + s];
+      }
+      const double m0 = shfl(m, base);
+#pragma unroll
+      for (int r = 1; r <= RT; r++) {
+        int p = b + r;
+        if (p >= N) p -= N;
+        double mp = shfl(m, base + p);
+        const double k = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+        if (take) kc[r - 1] = k;
+      }
+      double an[3], jn[3], q2, d2[RT];
+      ring_accjerk<N, false>(x, v, m, b, base, an, jn, q2, d2);
+      if (take) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          a0[c] = an[c];
+          j0[c] = jn[c];
+        }
+        t0 = B.t[s];
+        t = t0;
+        steps = 0;
+        const bool runnable = B.status[s] <= SWARM_SYS_DONE;
+        bool go;
+        if (!ADAPT) {
+          plan = launch_plan(B, P, s, t0, runnable);
+          go = runnable && plan.N > 0;
+        } else {
+          te = adaptive_end(B, P, s);
+          go = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
+        }
+        has = go;
+        if (runnable && !go && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
+      }
+      continue;
+    }
+    if (!__any_sync(FULL, has)) break;
+
+    // ---- one step for every group holding a system
+    const bool alive = has;
+    HCoef C;
+    bool last, bad = false;
+    double h = 0.0;
+    if (!ADAPT) {
+      last = steps + 1 == plan.N;
+      C = (last && !plan.exact) ? hcoef(plan.h_last) : cdt;
+    } else {
+      const double ratio = (j0[0] * j0[0] + j0[1] * j0[1] + j0[2] * j0[2]) / (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
+      const double ssum = grp_sum<N>(ratio, b, base);
+      h = tau * rsqrt(ssum);
+      const double rem = (te - t) * dir;
+      last = h >= rem;
+      bad = !(h > 0.0) || nonfinite(h);
+      h = (last ? rem : h) * dir;
+      C = hcoef(h);
+    }
+    double xk[3], vk[3], Xb[3], Vb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      xk[c] = fma(j0[c], C.h3_6, fma(a0[c], C.h2_2, fma(v[c], C.h, x[c])));
+      vk[c] = fma(j0[c], C.h2_2, fma(a0[c], C.h, v[c]));
+      Vb[c] = fma(j0[c], C.h2_12, fma(a0[c], C.hh, v[c]));
+    }
+    PCoef PC;
+    if (printed) {
+      PC = pcoef(C.h);
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(j0[c], PC.pj, fma(a0[c], PC.pa, xk[c]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xb[c] = fma(a0[c], C.h2_12, fma(v[c], C.hh, x[c]));
+    }
+    double q2, d2[RT];
+    for (int ic = 0; ic < P.n_corr; ic++) {
+      double ak[3], jk[3];
+      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+#pragma unroll
+      for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
+      if (printed) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(PC.cj, jk[c], fma(PC.ca, ak[c], Xb[c]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; c++) xk[c] = fma(-C.h2_12, ak[c], fma(C.hh, vk[c], Xb[c]));
+      }
+    }
+    double an[3], jn[3];
+    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    const bool active = alive && !bad;
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        x[c] = xk[c];
+        v[c] = vk[c];
+        a0[c] = an[c];
+        j0[c] = jn[c];
+      }
+      steps++;
+      if (!ADAPT) t = step_time(plan, steps, t0, P.dt);
+      else t = last ? te : t + h;
+    }
+    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
+                    nonfinite(v[2]);
+    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+    bool ce = false;
+#pragma unroll
+    for (int r = 1; r <= RT; r++) {
+      int p = b + r;
+      if (p >= N) p -= N;
+      double q2p = shfl(q2, base + p);
+      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+    }
+    const unsigned bnf = __ballot_sync(FULL, alive && (nf || bad)) & gm;
+    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+    int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    if (!alive) code = 0;
+    const bool reached = active && last && !code;
+    if (P.log_interval > 0) {
+      const bool need_log = active && !code && (steps % P.log_interval) == 0;
+      if (__any_sync(FULL, need_log)) {
+        double e4[4];
+        ring_energy<N>(x, v, m, b, base, e4);
+        if (need_log && lane_ok && b == 0) write_log(P, B.gidx[s], t, e4);
+      }
+    }
+    const bool capped = ADAPT && active && steps >= cap;
+    const bool finish = alive && (code != 0 || reached || capped);
+    if (finish && lane_ok) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + b) * SP + s] = x[c];
+        B.v[(size_t)(c * N + b) * SP + s] = v[c];
+      }
+      if (b == 0) {
+        B.t[s] = t;
+        if (code) B.status[s] = code;
+        else if (ADAPT) B.status[s] = reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+        else B.status[s] = plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+        if (P.counters && steps > 0) {
+          atomicAdd(&P.counters[0], (unsigned long long)steps);
+          atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps * (P.n_corr + 1)));
+        }
+      }
+    }
+    if (finish) has = false;
+  }
+}
+
 // Out-of-line copies called by the multi-body-count dispatcher kernel.
 template <int N>
 __device__ __noinline__ void bpl_hermite_unit(const BinView &B, const StepParams &P, int unit) {
@@ -791,6 +998,10 @@ template <int MAP, int N, int MINB, bool ADAPT = false>
 __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, int nunits, StepParams P) {
   if (ADAPT && MAP == SWARM_MAP_SYSTEM_PER_LANE) {  // work unit = system (per-lane refill)
     spl_hermite_adaptive_stream<N>(B, P);
+    return;
+  }
+  if (MAP == SWARM_MAP_BODY_PER_LANE) {  // work unit = system (per-group refill)
+    bpl_hermite_stream<N, ADAPT>(B, P);
     return;
   }
   const int lane = threadIdx.x & 31;
