@@ -295,6 +295,10 @@ def secondary(S, torch, stream):
     out["c2_persistent_500"] = timed(c2, 500 * DT, S.HERMITE4, DT)
     out["c2_persistent_body_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_BODY_PER_LANE)
     out["c2_persistent_system_per_lane_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE)
+    out["c2_persistent_system_per_lane_1cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE,
+                                                          ctas=1)
+    out["c2_persistent_body_per_lane_1cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_BODY_PER_LANE,
+                                                        ctas=1)
     out["c2_persistent_system_per_lane_3cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE,
                                                           ctas=3)
     c3 = ics.ragged(65536, seed=3)
@@ -302,6 +306,7 @@ def secondary(S, torch, stream):
     out["c3_ragged_hermite_single_launch_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT, single=1)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
+    out["c4_mvs_jacobi_2000_steps_1cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=1)
     out["c4_mvs_jacobi_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, outcome=True)
     out["c4_mvs_jacobi_1e5_steps_1cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=1)
     out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)

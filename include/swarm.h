@@ -190,8 +190,10 @@ void swarm_destroy_ensemble(swarm_ensemble *ens);
  * each swarm_server_step (1) admits queued requests, in arrival order, whose pool
  * (integrator, n) has enough free slots — pools are allocated on demand within
  * device_bytes (0 = no budget), empty pools are released when the budget is short —
- * (2) advances every occupied slot by at most quantum_steps steps toward its own t_end in
- * one persistent launch per integrator, and (3) retires requests whose systems all reached
+ * (2) advances every occupied slot by at most quantum_steps steps toward its own t_end
+ * (one launch per pool over the list of its occupied slots, body per lane, slots handed
+ * out per group; the pools' launches run concurrently), and (3) retires requests whose
+ * systems all reached
  * t_end or stopped, copying their results to host memory and freeing their slots for
  * the next admissions.  A system takes the same steps as it would alone (steps of dt, the
  * last one shortened to land on t_end), so results do not depend on the mix.  Not

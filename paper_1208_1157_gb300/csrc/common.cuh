@@ -28,7 +28,15 @@ struct BinView {
   int32_t *status;
   int32_t *gidx;  // ensemble-wide index of bin system s (log buffer rows)
   const double *t_end = nullptr;  // per-system end time (serving slots); null: the call's
+  const int32_t *list = nullptr;  // systems to run (serving: the occupied slots); null: all S
+  int nlist = 0;
 };
+
+// k-th system of a launch that hands out systems one by one, or -1 past the end
+__device__ __forceinline__ int stream_system(const BinView &B, int k) {
+  if (B.list) return k < B.nlist ? B.list[k] : -1;
+  return k < B.S ? k : -1;
+}
 
 struct StepParams {
   double t_end, dt;

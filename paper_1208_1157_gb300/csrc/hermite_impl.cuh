@@ -625,8 +625,8 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
   bool has = false, exhausted = false;
   for (;;) {
     if (!has && !exhausted) {
-      s = atomicAdd(P.work_next, 1);
-      if (s >= B.S) {
+      s = stream_system(B, atomicAdd(P.work_next, 1));
+      if (s < 0) {
         exhausted = true;
       } else if (B.status[s] <= SWARM_SYS_DONE) {
 #pragma unroll
@@ -803,7 +803,8 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
   plan.exact = 1;
   plan.h_last = P.dt;
   plan.t_end = P.t_end;
-  double t = 0.0, t0 = 0.0, te = 0.0;
+  HCoef clast = cdt;  // coefficients of a shortened last step (fixed steps)
+  double t = 0.0, t0 = 0.0, te = 0.0;  // fixed steps: t is formed from t0 when needed
   int steps = 0;
 #pragma unroll
   for (int r = 0; r < RT; r++) kc[r] = 0.0;
@@ -815,10 +816,11 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
       int sn = 0;
       if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
       sn = __shfl_sync(FULL, sn, base);
-      const bool take = need && sn < B.S;
-      if (need && sn >= B.S) exhausted = true;
+      const int ss = stream_system(B, sn);
+      const bool take = need && ss >= 0;
+      if (need && ss < 0) exhausted = true;
       if (take) {
-        s = sn;
+        s = ss;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           x[c] = B.x[(size_t)(c * N + b) * SP + s];
@@ -851,6 +853,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
         if (!ADAPT) {
           plan = launch_plan(B, P, s, t0, runnable);
           go = runnable && plan.N > 0;
+          clast = hcoef(plan.exact ? P.dt : plan.h_last);
         } else {
           te = adaptive_end(B, P, s);
           go = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
@@ -869,7 +872,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
     double h = 0.0;
     if (!ADAPT) {
       last = steps + 1 == plan.N;
-      C = (last && !plan.exact) ? hcoef(plan.h_last) : cdt;
+      C = hsel(last, clast, cdt);
     } else {
       const double ratio = (j0[0] * j0[0] + j0[1] * j0[1] + j0[2] * j0[2]) / (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
       const double ssum = grp_sum<N>(ratio, b, base);
@@ -922,8 +925,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
         j0[c] = jn[c];
       }
       steps++;
-      if (!ADAPT) t = step_time(plan, steps, t0, P.dt);
-      else t = last ? te : t + h;
+      if (ADAPT) t = last ? te : t + h;
     }
     const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
                     nonfinite(v[2]);
@@ -942,6 +944,10 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
     int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (!alive) code = 0;
     const bool reached = active && last && !code;
+    const bool capped = ADAPT && active && steps >= cap;
+    const bool finish = alive && (code != 0 || reached || capped);
+    if (!ADAPT && (finish || (P.log_interval > 0 && active && (steps % P.log_interval) == 0)))
+      t = step_time(plan, steps, t0, P.dt);
     if (P.log_interval > 0) {
       const bool need_log = active && !code && (steps % P.log_interval) == 0;
       if (__any_sync(FULL, need_log)) {
@@ -950,8 +956,6 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
         if (need_log && lane_ok && b == 0) write_log(P, B.gidx[s], t, e4);
       }
     }
-    const bool capped = ADAPT && active && steps >= cap;
-    const bool finish = alive && (code != 0 || reached || capped);
     if (finish && lane_ok) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {

@@ -14,8 +14,9 @@ __global__ void __launch_bounds__(kWideWarps * 32, 2) hermite_wide_kernel(BinVie
     int w = 0;
     if (lane == 0) w = atomicAdd(P.work_next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= B.S) break;
-    wide_hermite_body<ADAPT>(B, P, w, kc_s[wid], d2_s[wid]);
+    const int s = stream_system(B, w);
+    if (s < 0) break;
+    wide_hermite_body<ADAPT>(B, P, s, kc_s[wid], d2_s[wid]);
   }
 }
 

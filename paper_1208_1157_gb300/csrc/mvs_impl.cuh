@@ -578,9 +578,10 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       int sn = 0;
       if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
       sn = __shfl_sync(FULL, sn, base);
-      const bool take = need && sn < B.S;
-      if (need && sn >= B.S) exhausted = true;
-      const int sl = take ? sn : s;  // a valid row for every lane's loads
+      const int ss = stream_system(B, sn);
+      const bool take = need && ss >= 0;
+      if (need && ss < 0) exhausted = true;
+      const int sl = take ? ss : s;  // a valid row for every lane's loads
       double xn[3], vn[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -619,7 +620,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       for (int r = 0; r < RTA; r++) d2n[r] = 0.0;
       mvs_acc<N, JAC>(qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n);
       if (take) {
-        s = sn;
+        s = ss;
         const double tn = B.t[s];
         const bool runnable = B.status[s] <= SWARM_SYS_DONE;
         plan = launch_plan(B, P, s, tn, runnable);

@@ -343,10 +343,11 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
       int sn = 0;
       if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
       sn = __shfl_sync(FULL, sn, base);
-      const bool take = need && sn < B.S;
-      if (need && sn >= B.S) exhausted = true;
+      const int ss = stream_system(B, sn);
+      const bool take = need && ss >= 0;
+      if (need && ss < 0) exhausted = true;
       if (take) {
-        s = sn;
+        s = ss;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           x[c] = B.x[(size_t)(c * N + b) * SP + s];
@@ -431,8 +432,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
         a1[c] = an[c];
       }
       steps++;
-      if (!ADAPT) t = step_time(plan, steps, t0, P.dt);
-      else t = last ? te : t + hs;
+      if (ADAPT) t = last ? te : t + hs;
     }
     const double dq0 = x[0] - shfl(x[0], base), dq1 = x[1] - shfl(x[1], base), dq2 = x[2] - shfl(x[2], base);
     const double q2 = dq0 * dq0 + dq1 * dq1 + dq2 * dq2;
@@ -453,6 +453,8 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
     int code = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (!alive) code = 0;
     bool reached = accept && last && !code;
+    if (!ADAPT && accept && (code || reached || (P.log_interval > 0 && (steps % P.log_interval) == 0)))
+      t = step_time(plan, steps, t0, P.dt);  // fixed steps: time formed when it is used
     if (P.log_interval > 0) {
       const bool need_log = accept && !code && (steps % P.log_interval) == 0;
       if (__any_sync(FULL, need_log)) {

@@ -2,7 +2,8 @@
 // integrators share the GPU.  Their systems occupy slots of device-resident pools (one
 // pool per integrator and body count); every scheduling round admits queued requests
 // into free slots (within a device-memory budget), advances all occupied slots by one
-// quantum of at most Q steps in one persistent launch per integrator, then retires the
+// quantum of at most Q steps (one launch per pool over the list of its occupied slots,
+// the pools' launches running concurrently on forked streams), then retires the
 // requests whose systems all reached their end time or stopped and frees their slots for
 // the next admissions.  A request's systems take exactly the steps they would take alone
 // (full steps of dt, the last one shortened to land on its t_end), so its result does not
@@ -43,15 +44,25 @@ int sfail(int rc, const std::string &m) {
 
 struct Pool {
   int integ = 0, n = 0, cap = 0;
-  int mapping = SWARM_MAP_BODY_PER_LANE, per = 1;  // thread mapping, systems per work unit
   void *block = nullptr;
   BinView view{};
   double *t_end = nullptr;
-  std::set<int> free_slots;    // lowest slots are handed out first (dense work units)
+  std::set<int> free_slots;    // lowest slots are handed out first
   std::vector<int64_t> owner;  // request id per slot, -1 if free
-  std::vector<int> unit_occ;   // occupied slots per work unit
+  int32_t *d_list = nullptr;   // occupied slots of the current round (device)
+  std::vector<int32_t> h_list;
+  int *d_next = nullptr;       // work counter of the pool's launch
+  int blocks = 0;              // resident CTAs per SM of the pool's kernel
   size_t bytes = 0;
 };
+
+void free_pool(Pool *q) {
+  cudaFree(q->block);
+  cudaFree(q->d_list);
+  cudaFree(q->d_next);
+}
+
+constexpr int kSide = 8;  // forked streams for the pools' concurrent launches
 
 struct Request {
   int64_t id = 0;
@@ -121,21 +132,19 @@ struct swarm_server {
   int *d_slots = nullptr;
   size_t stage_doubles = 0;
   std::vector<int32_t> h_status;
-  // per-integrator launch resources
-  struct Launch {
-    BinView *d_bins = nullptr;
-    int4 *d_work = nullptr;
-    int nwork = 0, nbins = 0, cap_work = 0, cap_bins = 0;
-    int *d_next = nullptr;
-    bool dirty = true;
-  } launch[4];
+  // concurrent launches of the pools: side streams forked from and joined to `stream`
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t side_done[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
   unsigned long long *d_counters = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   swarm_server_stats stats{};
 };
 
+// device bytes of a pool: state (7n + 2 doubles per slot), status and index (2 ints per
+// slot), the slot list of a round (1 int per slot) and the work counter
 static size_t pool_bytes(int n, int cap) {
-  return sizeof(double) * (size_t)cap * (7 * n + 2) + 2 * sizeof(int32_t) * (size_t)cap;
+  return sizeof(double) * (size_t)cap * (7 * n + 2) + 3 * sizeof(int32_t) * (size_t)cap + sizeof(int);
 }
 
 static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
@@ -154,9 +163,8 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
     for (auto jt = sv->pools.begin(); jt != sv->pools.end();) {
       Pool *q = jt->second.get();
       if ((int)q->free_slots.size() == q->cap && sv->bytes_used + bytes > (size_t)sv->cfg.device_bytes) {
-        cudaFree(q->block);
+        free_pool(q);
         sv->bytes_used -= q->bytes;
-        sv->launch[q->integ].dirty = true;
         jt = sv->pools.erase(jt);
       } else {
         ++jt;
@@ -187,58 +195,18 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
   SCK(cudaGetLastError());
   for (int i = 0; i < cap; i++) p->free_slots.insert(p->free_slots.end(), i);
   p->owner.assign(cap, -1);
-  int32_t mapping = SWARM_MAP_BODY_PER_LANE, ctas = 0;
-  int rc = tuner_choice_internal(n, integ, cap, sv->stream, &mapping, &ctas);
-  if (rc) return rc;
-  if (integ != SWARM_HERMITE4 || n > 4) mapping = SWARM_MAP_BODY_PER_LANE;
-  p->mapping = mapping;
-  p->per = mapping == SWARM_MAP_SYSTEM_PER_LANE ? 32 : 32 / n;
-  p->unit_occ.assign((cap + p->per - 1) / p->per, 0);
+  SCK(cudaMalloc(&p->d_list, sizeof(int32_t) * cap));
+  SCK(cudaMalloc(&p->d_next, sizeof(int)));
+  p->h_list.reserve(cap);
+  // body-per-lane kernels that take the slot list and hand slots out per group
+  StepParams Q{};
+  Q.integrator = integ;
+  if (integ == SWARM_HERMITE4) SCK(launch_hermite_uniform(SWARM_MAP_BODY_PER_LANE, p->view, 0, Q, 0, sv->stream, &p->blocks, 0));
+  else SCK(launch_mvs_uniform(integ == SWARM_MVS_JACOBI, p->view, 0, Q, 0, sv->stream, &p->blocks));
+  if (p->blocks <= 0) return sfail(SWARM_ECUDA, "pool kernel cannot be resident");
   sv->bytes_used += bytes;
-  sv->launch[integ].dirty = true;
   *out = p.get();
   sv->pools[key] = std::move(p);
-  return SWARM_OK;
-}
-
-static int rebuild_launch(swarm_server *sv, int integ) {
-  auto &L = sv->launch[integ];
-  std::vector<Pool *> pools;
-  for (auto &kv : sv->pools)
-    if (kv.second->integ == integ) pools.push_back(kv.second.get());
-  if (L.dirty) {
-    std::vector<BinView> views;
-    for (Pool *p : pools) views.push_back(p->view);
-    if ((int)views.size() > L.cap_bins) {
-      if (L.d_bins) cudaFree(L.d_bins);
-      L.d_bins = nullptr;
-      SCK(cudaMalloc(&L.d_bins, sizeof(BinView) * std::max<size_t>(views.size(), 16)));
-      L.cap_bins = (int)std::max<size_t>(views.size(), 16);
-    }
-    if (!L.d_next) SCK(cudaMalloc(&L.d_next, sizeof(int)));
-    if (!views.empty())
-      SCK(cudaMemcpyAsync(L.d_bins, views.data(), sizeof(BinView) * views.size(), cudaMemcpyHostToDevice, sv->stream));
-    SCK(cudaStreamSynchronize(sv->stream));
-    L.nbins = (int)views.size();
-    L.dirty = false;
-  }
-  // only the work units that hold an occupied slot, heaviest body count first
-  std::vector<int4> work;
-  for (size_t b = 0; b < pools.size(); b++) {
-    Pool *p = pools[b];
-    for (int u = 0; u < (int)p->unit_occ.size(); u++)
-      if (p->unit_occ[u]) work.push_back(make_int4((int)b, u, p->mapping, p->n));
-  }
-  std::stable_sort(work.begin(), work.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
-  if ((int)work.size() > L.cap_work) {
-    if (L.d_work) cudaFree(L.d_work);
-    L.d_work = nullptr;
-    SCK(cudaMalloc(&L.d_work, sizeof(int4) * work.size()));
-    L.cap_work = (int)work.size();
-  }
-  if (!work.empty())
-    SCK(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice, sv->stream));
-  L.nwork = (int)work.size();
   return SWARM_OK;
 }
 
@@ -258,6 +226,11 @@ extern "C" int swarm_server_create(const swarm_server_config *cfg, void *cuda_st
   SCK(cudaMalloc(&sv->d_counters, sizeof(unsigned long long) * 4));
   SCK(cudaEventCreate(&sv->ev0));
   SCK(cudaEventCreate(&sv->ev1));
+  SCK(cudaEventCreateWithFlags(&sv->fork_ev, cudaEventDisableTiming));
+  for (int i = 0; i < kSide; i++) {
+    SCK(cudaStreamCreateWithFlags(&sv->side[i], cudaStreamNonBlocking));
+    SCK(cudaEventCreateWithFlags(&sv->side_done[i], cudaEventDisableTiming));
+  }
   *out = sv.release();
   return SWARM_OK;
 }
@@ -266,12 +239,12 @@ extern "C" void swarm_server_destroy(swarm_server *sv) {
   if (!sv) return;
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   else cudaDeviceSynchronize();
-  for (auto &kv : sv->pools) cudaFree(kv.second->block);
-  for (auto &L : sv->launch) {
-    if (L.d_bins) cudaFree(L.d_bins);
-    if (L.d_work) cudaFree(L.d_work);
-    if (L.d_next) cudaFree(L.d_next);
+  for (auto &kv : sv->pools) free_pool(kv.second.get());
+  for (int i = 0; i < kSide; i++) {
+    if (sv->side[i]) cudaStreamDestroy(sv->side[i]);
+    if (sv->side_done[i]) cudaEventDestroy(sv->side_done[i]);
   }
+  if (sv->fork_ev) cudaEventDestroy(sv->fork_ev);
   cudaFree(sv->d_stage);
   cudaFree(sv->d_slots);
   cudaFree(sv->d_counters);
@@ -328,7 +301,6 @@ static int admit(swarm_server *sv) {
       p->free_slots.erase(p->free_slots.begin());
       r->slots[i] = slot;
       p->owner[slot] = r->id;
-      p->unit_occ[slot / p->per]++;
     }
     r->pool = p;
     const size_t nb = (size_t)r->n_sys * r->n;
@@ -394,7 +366,6 @@ static int retire(swarm_server *sv, int32_t *n_completed) {
     for (int s : r->slots) {
       p->owner[s] = -1;
       p->free_slots.insert(s);
-      p->unit_occ[s / p->per]--;
     }
     r->slots.clear();
     r->state = SWARM_REQ_DONE;
@@ -413,32 +384,52 @@ extern "C" int swarm_server_step(swarm_server *sv, int32_t *n_completed) {
   bool ran = false;
   SCK(cudaMemsetAsync(sv->d_counters, 0, sizeof(unsigned long long) * 4, sv->stream));
   SCK(cudaEventRecord(sv->ev0, sv->stream));
-  for (int integ = SWARM_HERMITE4; integ <= SWARM_MVS_JACOBI; integ++) {
-    bool occupied = false;
-    for (auto &kv : sv->pools)
-      if (kv.second->integ == integ && (int)kv.second->free_slots.size() < kv.second->cap) occupied = true;
-    if (!occupied) continue;
-    if ((rc = rebuild_launch(sv, integ))) return rc;
-    auto &L = sv->launch[integ];
-    if (L.nwork == 0) continue;
-    StepParams P{};
-    P.t_end = 0;
-    P.dt = integ == SWARM_HERMITE4 ? sv->cfg.hermite_dt : sv->cfg.mvs_dt;
-    P.n_corr = 2;
-    P.integrator = integ;
-    P.ce_factor = sv->cfg.ce_hill_factor;
-    P.eject2 = sv->cfg.eject_radius > 0 ? sv->cfg.eject_radius * sv->cfg.eject_radius : 0.0;
-    P.counters = sv->d_counters;
-    P.work_next = L.d_next;
-    P.max_steps = sv->cfg.quantum_steps;
-    int maxb = integ == SWARM_HERMITE4 ? hermite_persistent_max_blocks_per_sm() : mvs_persistent_max_blocks_per_sm();
+  // pools with occupied slots, heaviest body count first
+  std::vector<Pool *> run;
+  for (auto &kv : sv->pools)
+    if ((int)kv.second->free_slots.size() < kv.second->cap) run.push_back(kv.second.get());
+  std::stable_sort(run.begin(), run.end(), [](const Pool *a, const Pool *b) { return a->n > b->n; });
+  if (!run.empty()) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = std::max(1, std::min(sms * std::max(maxb, 1), (L.nwork + 3) / 4));
-    SCK(cudaMemsetAsync(L.d_next, 0, sizeof(int), sv->stream));
-    if (integ == SWARM_HERMITE4) SCK(launch_hermite_persistent(L.d_bins, L.d_work, L.nwork, P, grid, sv->stream));
-    else SCK(launch_mvs_persistent(L.d_bins, L.d_work, L.nwork, P, grid, sv->stream));
+    const int K = std::min((int)run.size(), kSide);
+    SCK(cudaEventRecord(sv->fork_ev, sv->stream));
+    for (int j = 0; j < K; j++) SCK(cudaStreamWaitEvent(sv->side[j], sv->fork_ev, 0));
+    for (size_t i = 0; i < run.size(); i++) {
+      Pool *p = run[i];
+      cudaStream_t st = sv->side[i % K];
+      p->h_list.clear();
+      for (int slot = 0; slot < p->cap; slot++)
+        if (p->owner[slot] >= 0) p->h_list.push_back(slot);
+      const int nl = (int)p->h_list.size();
+      SCK(cudaMemcpyAsync(p->d_list, p->h_list.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, st));
+      SCK(cudaMemsetAsync(p->d_next, 0, sizeof(int), st));
+      StepParams P{};
+      P.t_end = 0;
+      P.dt = p->integ == SWARM_HERMITE4 ? sv->cfg.hermite_dt : sv->cfg.mvs_dt;
+      P.n_corr = 2;
+      P.integrator = p->integ;
+      P.ce_factor = sv->cfg.ce_hill_factor;
+      P.eject2 = sv->cfg.eject_radius > 0 ? sv->cfg.eject_radius * sv->cfg.eject_radius : 0.0;
+      P.counters = sv->d_counters;
+      P.work_next = p->d_next;
+      P.max_steps = sv->cfg.quantum_steps;
+      BinView v = p->view;
+      v.list = p->d_list;
+      v.nlist = nl;
+      const int per = 32 / p->n;
+      const int nunits = (nl + per - 1) / per;
+      const int grid = std::max(1, std::min(sms * p->blocks, (nunits + 3) / 4));
+      if (p->integ == SWARM_HERMITE4)
+        SCK(launch_hermite_uniform(SWARM_MAP_BODY_PER_LANE, v, nunits, P, grid, st, nullptr, 0));
+      else
+        SCK(launch_mvs_uniform(p->integ == SWARM_MVS_JACOBI, v, nunits, P, grid, st, nullptr));
+    }
+    for (int j = 0; j < K; j++) {
+      SCK(cudaEventRecord(sv->side_done[j], sv->side[j]));
+      SCK(cudaStreamWaitEvent(sv->stream, sv->side_done[j], 0));
+    }
     ran = true;
   }
   SCK(cudaEventRecord(sv->ev1, sv->stream));
@@ -497,7 +488,6 @@ extern "C" int swarm_server_cancel(swarm_server *sv, int64_t id) {
     for (int sl : r->slots) {
       p->owner[sl] = -1;
       p->free_slots.insert(sl);
-      p->unit_occ[sl / p->per]--;
     }
     r->slots.clear();
   }

@@ -91,7 +91,7 @@ def test_memory_budget_releases_idle_pools():
     trace = [{"id": r, "arrival_s": 0.0, "n_sys": 20, "n": n, "integrator": 1, "t_end": 30 * HDT, "seed": 3000 + r}
              for r, n in enumerate([3, 4, 6, 7])]
     ens_list = [ics.request_ensemble(q) for q in trace]
-    one_pool = 32 * (7 * 7 + 2) * 8 + 2 * 4 * 32  # the largest of these pools (n = 7, 32 slots)
+    one_pool = 32 * (7 * 7 + 2) * 8 + 3 * 4 * 32 + 4  # the largest of these pools (n = 7, 32 slots)
     with SV.Server(slots_per_pool=32, quantum_steps=10, device_bytes=one_pool) as sv:
         out = SV.replay(sv, trace, ens_list, collect=True)
         st = sv.stats()
