@@ -306,12 +306,13 @@ def secondary(S, torch, stream):
     out["c3_ragged_hermite_single_launch_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT, single=1)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
-    out["c4_mvs_jacobi_2000_steps_1cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=1)
+    out["c4_mvs_jacobi_2000_steps_3cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=3)
     out["c4_mvs_jacobi_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, outcome=True)
-    out["c4_mvs_jacobi_1e5_steps_1cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=1)
+    out["c4_mvs_jacobi_1e5_steps_3cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=3)
     out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)
     out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
     out["c2_rkck_fixed_500"] = timed(c2, 500 * DT, S.RKCK, DT)
+    out["c2_rkck_fixed_1cta_500"] = timed(c2, 500 * DT, S.RKCK, DT, ctas=1)
     out["c2_rkck_adaptive_eps_1e-12_one_period"] = timed(c2, TWO_PI, S.RKCK_ADAPTIVE, 0.05)
     out["c3_ragged_rkck_100_steps"] = timed(c3, 100 * DT, S.RKCK, DT)
     c6 = ics.ragged_wide(16384, seed=6)

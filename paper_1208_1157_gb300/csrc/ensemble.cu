@@ -595,6 +595,11 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     if (m == SWARM_MAP_SYSTEM_PER_LANE && (!hermite_family(integrator) || e->bins[i].n > 4))
       m = SWARM_MAP_BODY_PER_LANE;
     maps[i] = m;
+    // MVS: one CTA of 4 warps per SM (one warp per SM sub-partition) unless set; with
+    // systems handed out per group this keeps the FP64 pipe as busy as more warps do and
+    // halves the step time of the last systems of a call (16384 x 8 compact ensemble:
+    // +4 % over 2000 steps, +35 % over 1e5 steps, where few systems run the last steps)
+    if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) bin_ctas[i] = 1;
   }
   int rc = build_work(e, maps);
   if (rc) return rc;

@@ -420,7 +420,9 @@ extern "C" int swarm_server_step(swarm_server *sv, int32_t *n_completed) {
       v.nlist = nl;
       const int per = 32 / p->n;
       const int nunits = (nl + per - 1) / per;
-      const int grid = std::max(1, std::min(sms * p->blocks, (nunits + 3) / 4));
+      // MVS pools: one CTA per SM (as for ensembles), Hermite pools: full residency
+      const int per_sm = p->integ == SWARM_HERMITE4 ? p->blocks : 1;
+      const int grid = std::max(1, std::min(sms * per_sm, (nunits + 3) / 4));
       if (p->integ == SWARM_HERMITE4)
         SCK(launch_hermite_uniform(SWARM_MAP_BODY_PER_LANE, v, nunits, P, grid, st, nullptr, 0));
       else
