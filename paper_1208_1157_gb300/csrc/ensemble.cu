@@ -624,7 +624,8 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = units_of(u.view.n, u.view.S, u.mapping);
       int blocks = 0;
       u.variant = bin_ctas[i] == 3 ? 1 : 0;
-      if (u.mapping == kMapWide) CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
+      if (u.mapping == kMapWide && rkck_family(integrator)) CK(launch_rkck_wide(u.view, P, 0, e->stream, &blocks));
+      else if (u.mapping == kMapWide) CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
       else if (hermite_family(integrator)) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
       else if (rkck_family(integrator)) CK(launch_rkck_uniform(u.view, u.nunits, P, 0, e->stream, &blocks));
       else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, P, 0, e->stream, &blocks));
@@ -641,7 +642,8 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = u.view.S;
       u.variant = 0;
       int blocks = 0;
-      CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
+      if (rkck_family(integrator)) CK(launch_rkck_wide(u.view, P, 0, e->stream, &blocks));
+      else CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
       if (blocks <= 0) return fail(SWARM_ECUDA, "wide kernel cannot be resident");
       u.grid = std::max(1, std::min(sms * blocks, (u.nunits + 3) / 4));
       uni.push_back(u);
@@ -674,7 +676,9 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       StepParams Qi = Q;
       Qi.work_next = e->d_work_next + 1 + i;
       CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), si));
-      if (uni[i].mapping == kMapWide)
+      if (uni[i].mapping == kMapWide && rkck_family(integrator))
+        CK(launch_rkck_wide(uni[i].view, Qi, uni[i].grid, si, nullptr));
+      else if (uni[i].mapping == kMapWide)
         CK(launch_hermite_wide(uni[i].view, Qi, uni[i].grid, si, nullptr));
       else if (hermite_family(integrator))
         CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, si, nullptr,
@@ -735,11 +739,11 @@ static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, doubl
   if (!adaptive(integrator) && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
   if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && (integrator != SWARM_HERMITE4 || e->corr_form))
     return fail(SWARM_EINVAL, "the plain per-step baseline exists for the fixed-step time-symmetric Hermite only");
-  if (!hermite_family(integrator))
+  if (!hermite_family(integrator) && !rkck_family(integrator))
     for (auto &b : e->bins)
       if (b.n > SWARM_RING_MAX_N)
-        return fail(SWARM_EINVAL, "systems of more than %d bodies are integrated by the Hermite integrators only",
-                    SWARM_RING_MAX_N);
+        return fail(SWARM_EINVAL, "systems of more than %d bodies are integrated by the Hermite and Runge-Kutta "
+                    "integrators only", SWARM_RING_MAX_N);
   StepParams P = make_params(e, t_end, integrator, dt);
   CK(cudaMemsetAsync(e->d_counters, 0, sizeof(unsigned long long) * 4, e->stream));
   e->launches = 0;

@@ -96,6 +96,52 @@ __device__ __forceinline__ void wring_accjerk(const double (&x)[3], const double
   }
 }
 
+// Acceleration only (Eq. 1) of body b, with the pair distances of each round in
+// d2s[(r - 1) * 32 + lane] (used by the monitor when the state is the accepted one).
+__device__ __forceinline__ void wring_acc(const double (&x)[3], double m, int b, const WideRing &R, double (&a)[3],
+                                          double *d2s, int lane) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) a[c] = 0.0;
+#pragma unroll
+  for (int r = 1; r <= kWideRounds; r++) {
+    if (r > R.RT) break;  // warp-uniform
+    const bool full = r <= R.RF;
+    int p = b + r;
+    if (p >= R.n) p -= R.n;
+    int q = b - r;
+    if (q < 0) q += R.n;
+    double dx[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], p) - x[c];
+    const double mp = shfl(m, p);
+    double r2 = dx[0] * dx[0];
+    r2 = fma(dx[1], dx[1], r2);
+    r2 = fma(dx[2], dx[2], r2);
+    const double rho = rsqrt(r2);
+    const double rho3 = rho * rho * rho;
+    const double sp = mp * rho3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
+    if (full) {  // reaction from lane q, which evaluated the pair (q, b)
+      const double si = m * rho3;
+      double rdx[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) rdx[c] = shfl(dx[c], q);
+      const double rs = shfl(si, q);
+#pragma unroll
+      for (int c = 0; c < 3; c++) a[c] = fma(-rs, rdx[c], a[c]);
+    }
+    d2s[(r - 1) * 32 + lane] = r2;
+  }
+}
+
+// maximum over the warp's 32 lanes (idle lanes pass 0), result in every lane
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
 // Energy (Eq. 6, pairs once) and angular momentum of the warp's system, in every lane.
 __device__ __forceinline__ void wring_energy(const double (&x)[3], const double (&v)[3], double m, int b, bool real,
                                              const WideRing &R, double (&out)[4]) {

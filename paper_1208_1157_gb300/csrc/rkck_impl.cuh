@@ -105,203 +105,16 @@ __device__ __forceinline__ void rkck_stages(const double (&x)[3], const double (
   }
 }
 
-// One work unit = one warp's G = 32/N systems of a bin, integrated for the whole call.
+// Body per lane: G = 32/N systems per warp, lane b of a group holds body b.  Work is
+// handed out per system: each group takes the bin's next system (a per-bin counter) as
+// soon as its own one has reached its end time or stopped, so groups whose systems need
+// fewer (adaptive) steps or stop early do not idle until the warp's last system is done.
+// A refill round loads the new systems and evaluates their first stage (the other groups
+// re-evaluate their unchanged state, which gives the same values).
 // ADAPT = false: fixed steps with the step-count rule of the fixed-step integrators.
-// ADAPT = true: the caller's dt is the first trial step; trials are accepted when the
-// scaled error max_b max(|ex_b|/X, |ev_b|/V) (X, V the largest body position and velocity
+// ADAPT = true: the caller's dt is the first trial step; a trial is accepted when the
+// scaled error max_b max(|ex_b|/X, |ev_b|/V) (X, V the largest body position and speed
 // at the step's start) is at most P.rk_eps; the next trial is h * clamp(0.9 err^(-1/5)).
-template <int N, bool ADAPT>
-__device__ __forceinline__ void bpl_rkck_body(const BinView &B, const StepParams &P, int unit) {
-  using R = ARing<N>;
-  constexpr int G = 32 / N;
-  constexpr int RT = R::RTA;
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  int g = lane / N, b = lane - g * N;
-  const bool lane_ok = g < G;
-  if (!lane_ok) {  // spare lanes mirror group 0 so every shuffle stays well defined
-    g = 0;
-    b = lane - G * N;
-  }
-  const int base = g * N;
-  const int s0 = unit * G;
-  int s = s0 + g;
-  const bool sys_ok = lane_ok && s < B.S;
-  if (s >= B.S) s = s0;
-  const int SP = B.S_pad;
-
-  double x[3], v[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    x[c] = B.x[(size_t)(c * N + b) * SP + s];
-    v[c] = B.v[(size_t)(c * N + b) * SP + s];
-  }
-  const double m = B.m[(size_t)b * SP + s];
-  const double t0 = B.t[s];
-  const int st0 = B.status[s];
-  const double m0 = shfl(m, base);
-  const bool runnable = sys_ok && st0 <= SWARM_SYS_DONE;
-
-  // fixed steps: the launch plan; adaptive: end time and direction
-  LaunchPlan plan;
-  double te, dir = 1.0;
-  bool alive;
-  int nmax;
-  if (!ADAPT) {
-    plan = launch_plan(B, P, s, t0, runnable);
-    te = plan.t_end;
-    alive = runnable && plan.N > 0;
-    nmax = __reduce_max_sync(FULL, plan.N);
-  } else {
-    te = B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
-    dir = P.dt > 0 ? 1.0 : -1.0;
-    alive = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
-    nmax = P.max_steps > 0 ? P.max_steps : kRkckTrialCap;
-  }
-  if (!__any_sync(FULL, alive)) {
-    if (runnable && b == 0) B.status[s] = SWARM_SYS_DONE;
-    return;
-  }
-
-  double kc[RT];
-#pragma unroll
-  for (int r = 1; r <= RT; r++) {
-    int p = b + r;
-    if (p >= N) p -= N;
-    double mp = shfl(m, base + p);
-    kc[r - 1] = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
-  }
-  double a1[3], d2[RT];
-  ring_acc<N, 0>(x, m, b, base, a1, d2);
-
-  const bool ran = alive;
-  double t = t0;
-  double h = fabs(P.dt);
-  int steps = 0, trials = 0, code = 0;
-  bool reached = false;
-  for (int k = 1; k <= nmax; k++) {
-    if (!__any_sync(FULL, alive)) break;
-    // this trial's step (group-uniform)
-    double hs;
-    bool last;
-    if (!ADAPT) {
-      last = k == plan.N;
-      hs = (last && !plan.exact) ? plan.h_last : P.dt;
-    } else {
-      const double rem = (te - t) * dir;
-      last = h >= rem;
-      hs = (last ? rem : h) * dir;
-    }
-    double x5[3], v5[3], ex[3], ev[3];
-    rkck_stages<N, ADAPT>(x, v, a1, m, b, base, hs, x5, v5, ex, ev);
-    bool accept = alive;
-    double err = 0.0;
-    bool bad = false;
-    if (ADAPT) {
-      const double X2 = grp_max<N>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2], b, base);
-      const double V2 = grp_max<N>(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], b, base);
-      const double px = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
-      const double pv = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
-      const double rq = grp_max<N>(fmax(px / X2, pv / V2), b, base);
-      err = sqrt(rq) / P.rk_eps;
-      bad = nonfinite(err);
-      accept = alive && !bad && err <= 1.0;
-      if (alive) trials++;
-    }
-    // next first stage (and the monitor's distances) at the accepted state; a rejected
-    // group re-evaluates its unchanged state
-    double xn[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) xn[c] = accept ? x5[c] : x[c];
-    double an[3];
-    ring_acc<N, 0>(xn, m, b, base, an, d2);
-    if (accept) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        x[c] = x5[c];
-        v[c] = v5[c];
-        a1[c] = an[c];
-      }
-      steps++;
-      if (!ADAPT) t = step_time(plan, k, t0, P.dt);
-      else t = last ? te : t + hs;
-    }
-    // monitor on the accepted state
-    const double dq0 = x[0] - shfl(x[0], base), dq1 = x[1] - shfl(x[1], base), dq2 = x[2] - shfl(x[2], base);
-    const double q2 = dq0 * dq0 + dq1 * dq1 + dq2 * dq2;
-    const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
-                    nonfinite(v[2]);
-    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
-    bool ce = false;
-#pragma unroll
-    for (int r = 1; r <= RT; r++) {
-      int p = b + r;
-      if (p >= N) p -= N;
-      double q2p = shfl(q2, base + p);
-      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
-    }
-    const unsigned gm = ((1u << N) - 1u) << base;
-    const unsigned bnf = __ballot_sync(FULL, (accept && nf) || (alive && bad)) & gm;
-    const unsigned bej = __ballot_sync(FULL, accept && ej) & gm;
-    const unsigned bce = __ballot_sync(FULL, accept && ce) & gm;
-    const int c2 = bnf ? SWARM_SYS_NONFINITE : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-    if (alive && c2) {
-      code = c2;
-      alive = false;
-    } else if (accept && last) {
-      reached = true;
-      alive = false;
-    }
-    if (P.log_interval > 0) {
-      const bool need = accept && !c2 && (steps % P.log_interval) == 0;
-      if (__any_sync(FULL, need)) {
-        double e4[4];
-        ring_energy<N>(x, v, m, b, base, e4);
-        if (need && b == 0 && sys_ok) write_log(P, B.gidx[s], t, e4);
-      }
-    }
-    if (ADAPT && alive) {
-      // step control (Hairer, Norsett & Wanner, Sec. II.4): safety 0.9, ratio in [0.2, 5]
-      double f;
-      if (err <= 1e-30) f = 5.0;
-      else if (err >= 1e30) f = 0.2;
-      else f = 0.9 * inv_fifth_root(err);
-      h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
-      if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) {  // step-size underflow
-        code = SWARM_SYS_NONFINITE;
-        alive = false;
-      }
-    }
-  }
-  if (sys_ok && ran) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      B.x[(size_t)(c * N + b) * SP + s] = x[c];
-      B.v[(size_t)(c * N + b) * SP + s] = v[c];
-    }
-    if (b == 0) {
-      B.t[s] = t;
-      if (ADAPT) B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
-      else B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
-    }
-  } else if (runnable && b == 0) {
-    B.status[s] = SWARM_SYS_DONE;  // already at its end time
-  }
-  if (P.counters && sys_ok && b == 0 && ran) {
-    constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
-    const unsigned long long tr = ADAPT ? (unsigned long long)trials : (unsigned long long)steps;
-    if (steps > 0) atomicAdd(&P.counters[0], (unsigned long long)steps);
-    atomicAdd(&P.counters[1], NP * (1ull + 6ull * tr));
-  }
-}
-
-// The same integration with work handed out per system: each of the warp's G groups
-// takes the bin's next system (a per-bin counter) as soon as its own one has reached its
-// end time or stopped, so groups whose systems need fewer (adaptive) steps or stop early
-// do not idle until the warp's last system is done.  A refill round loads the new
-// systems and evaluates their first stage (the other groups re-evaluate their unchanged
-// state, which gives the same values); per system the arithmetic is that of
-// bpl_rkck_body.
 template <int N, bool ADAPT>
 __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepParams &P) {
   using R = ARing<N>;

@@ -218,3 +218,17 @@ def test_printed_form_corrector_parity(mapping):
         e.integrate(1000 * DT, S.HERMITE4, DT)
         g = e.state()
     assert_parity(ens, g, o)
+
+
+def test_adaptive_full_size_sampled():
+    # the paper-shaped ensemble with Eq. 5 steps (tau = 0.01) over one inner period, in the
+    # benchmark's launch configuration (system per lane, systems handed out per lane)
+    ens = ics.three_body(131072, seed=2)
+    g = run_gpu(ens, TWO_PI, 4, 0.01, ce=3.0, ej=100.0)
+    idx = np.sort(np.random.default_rng(4).choice(131072, 32, replace=False))
+    sub = ics.subset(ens, idx)
+    o = run_oracle(sub, TWO_PI, O.HERMITE_ADAPTIVE, 0.01, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, TWO_PI, O.HERMITE_ADAPTIVE, 0.01, ce=3.0, ej=100.0)
+    gs = {"pos": g["pos"].reshape(-1, 3, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 3, 3)[idx].reshape(-1, 3),
+          "time": g["time"][idx], "status": g["status"][idx]}
+    assert_parity(sub, gs, o, sens=sens, steps=2000)

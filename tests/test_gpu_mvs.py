@@ -60,13 +60,13 @@ def test_mvs_shortened_last_step_and_log(kind):
 
 
 def test_mvs_full_size_sampled():
-    # 16384 x 8 bodies in the benchmark's launch configuration; 1000 steps, 24 samples
+    # 16384 x 8 bodies in the benchmark's launch configuration; 2000 steps, 24 samples
     ens = ics.mvs_compact(16384, seed=4)
-    g = run_gpu(ens, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, 2000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
     idx = np.sort(np.random.default_rng(2).choice(16384, 24, replace=False))
     sub = ics.subset(ens, idx)
-    o = run_oracle(sub, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
-    sens = oracle_sensitivity(sub, 1000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    o = run_oracle(sub, 2000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, 2000 * DT, O.MVS_JACOBI, DT, ce=3.0, ej=100.0)
     gs = {"pos": g["pos"].reshape(-1, 8, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 8, 3)[idx].reshape(-1, 3),
           "time": g["time"][idx], "status": g["status"][idx]}
     assert_parity(sub, gs, o, sens=sens)

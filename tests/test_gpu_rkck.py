@@ -90,3 +90,25 @@ def test_rkck_tolerance_is_checked():
         for bad in (0.0, -1e-9, 1.0, float("nan")):
             with pytest.raises(S.SwarmError):
                 e.set_tolerance(bad)
+
+
+def sample_rows(ens, g, idx):
+    n = int(ens["n_body"][0])
+    return {"pos": g["pos"].reshape(-1, n, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, n, 3)[idx].reshape(-1, 3),
+            "time": g["time"][idx], "status": g["status"][idx]}
+
+
+def test_rkck_full_size_sampled():
+    # the paper-shaped ensemble (131072 x 3) in the benchmark's launch configuration:
+    # 500 fixed steps and one inner period of adaptive steps, 32 sampled systems each
+    ens = ics.three_body(131072, seed=2)
+    idx = np.sort(np.random.default_rng(3).choice(131072, 32, replace=False))
+    sub = ics.subset(ens, idx)
+    g = run_gpu(ens, 500 * DT, RKCK, DT, ce=3.0, ej=100.0)
+    o = run_oracle(sub, 500 * DT, O.RKCK, DT, ce=3.0, ej=100.0)
+    assert_parity(sub, sample_rows(ens, g, idx), o, sens=oracle_sensitivity(sub, 500 * DT, O.RKCK, DT, ce=3.0, ej=100.0),
+                  steps=500)
+    g = run_gpu(ens, TWO_PI, RKCK_ADAPTIVE, 0.05, ce=3.0, ej=100.0)
+    o = run_oracle(sub, TWO_PI, O.RKCK_ADAPTIVE, 0.05, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, TWO_PI, O.RKCK_ADAPTIVE, 0.05, ce=3.0, ej=100.0)
+    assert_parity(sub, sample_rows(ens, g, idx), o, sens=sens, steps=1000, stop_time_rtol=1e-8)

@@ -74,9 +74,38 @@ def test_wide_logs_and_chunked_launches():
     assert ex.max() == 0.0 and ev.max() == 0.0
 
 
-def test_wide_systems_refuse_the_other_integrators():
+def test_wide_systems_refuse_mvs():
     from paper_1208_1157_gb300 import swarm as S
     with S.Ensemble(ics.ragged_wide(4, seed=36)) as e:
-        for integ in (S.MVS_DH, S.MVS_JACOBI, S.RKCK, S.RKCK_ADAPTIVE):
+        for integ in (S.MVS_DH, S.MVS_JACOBI):
             with pytest.raises(S.SwarmError):
                 e.integrate(0.1, integ, 0.01)
+
+
+def test_wide_runge_kutta_parity():
+    # fixed steps (shortened last one) and adaptive steps on 16..32-body systems, mixed
+    # with smaller ones in the same ensemble
+    ens = ics.concat(ics.ragged_wide(48, seed=37), ics.ragged(40, seed=38))
+    t_end = 80.5 * DT
+    o = run_oracle(ens, t_end, O.RKCK, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, t_end, O.RKCK, DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, t_end, 5, DT, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens, steps=81)
+    kw = dict(ce=3.0, ej=100.0, rk_eps=1e-11)
+    o = run_oracle(ens, 0.3 * TWO_PI, O.RKCK_ADAPTIVE, 0.05, **kw)
+    sens = oracle_sensitivity(ens, 0.3 * TWO_PI, O.RKCK_ADAPTIVE, 0.05, **kw)
+    g = run_gpu(ens, 0.3 * TWO_PI, 6, 0.05, **kw)
+    assert_parity(ens, g, o, sens=sens, steps=2000, stop_time_rtol=1e-8)
+
+
+def test_wide_full_size_sampled():
+    # the 16384-system 16..32-body ensemble of the benchmark, 20 steps, 24 sampled systems
+    ens = ics.ragged_wide(16384, seed=6)
+    g = run_gpu(ens, 20 * DT, 1, DT, ce=3.0, ej=100.0)
+    idx = np.sort(np.random.default_rng(5).choice(16384, 24, replace=False))
+    sub = ics.subset(ens, idx)
+    o = run_oracle(sub, 20 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    offs = np.concatenate([[0], np.cumsum(ens["n_body"])])
+    rows = np.concatenate([np.arange(offs[i], offs[i + 1]) for i in idx])
+    gs = {"pos": g["pos"][rows], "vel": g["vel"][rows], "time": g["time"][idx], "status": g["status"][idx]}
+    assert_parity(sub, gs, o, steps=20)
