@@ -232,3 +232,28 @@ def test_adaptive_full_size_sampled():
     gs = {"pos": g["pos"].reshape(-1, 3, 3)[idx].reshape(-1, 3), "vel": g["vel"].reshape(-1, 3, 3)[idx].reshape(-1, 3),
           "time": g["time"][idx], "status": g["status"][idx]}
     assert_parity(sub, gs, o, sens=sens, steps=2000)
+
+
+@pytest.mark.parametrize("single", [0, 1])
+def test_ragged_chunked_launches_with_forked_streams(single):
+    # several body counts: per-bin launches forked onto side streams (single = 0) or the
+    # shared launch next to the 16..32-body bins' launches (single = 1), captured into a
+    # graph in rounds of <= 40 steps; the result equals the one-round call bit for bit
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.concat(ics.ragged(260, seed=19), ics.ragged_wide(20, seed=20))
+    ref = run_gpu(ens, 200 * DT, 1, DT, ce=3.0, ej=100.0, single_launch=single)
+    with S.Ensemble(ens) as e:
+        e.set_stop(3.0, 100.0)
+        e.set_option(S.OPT_SINGLE_LAUNCH, single)
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, 40)
+        e.integrate(200 * DT, S.HERMITE4, DT)
+        launches = e.stats()["kernel_launches"]
+        got = e.state()
+    nbins = len(set(ens["n_body"].tolist()))
+    nwide = len(set(n for n in ens["n_body"].tolist() if n >= 16))
+    per_round = nbins if single == 0 else 1 + nwide
+    assert launches == 5 * per_round
+    assert np.array_equal(got["status"], ref["status"])
+    assert np.array_equal(got["time"], ref["time"])
+    assert np.array_equal(got["pos"], ref["pos"]) and np.array_equal(got["vel"], ref["vel"])
