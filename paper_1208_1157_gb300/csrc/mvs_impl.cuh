@@ -144,7 +144,10 @@ static __device__ __noinline__ double chi_guess(const KepConst &K, const double 
 
 // Universal-variable Kepler drift of (r, v) by h: Newton on
 //   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
-// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|); then the Lagrange f, g,
+// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|), or until the error left after
+// the step, which for Newton is (F''/2F') d chi^2 with F'' = s0 (1 - z c2) + beta chi
+// (1 - z c3), is below 1e-15 max(1, |chi|): the same root to the same tolerance, usually
+// one iteration sooner (the oracle only uses the first test); then the Lagrange f, g,
 // fdot, gdot.  `chi` carries the previous step's solution as the starting point (warm
 // start; `have_chi` false on the first step of a call).  Executed by every lane of the
 // warp; lanes with `on` false do not change their state.  Returns false on
@@ -173,11 +176,14 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
       stumpff23(z, c2, c3);
       double x3 = x2 * x;
       double F = fma(s0 * x2, c2, fma(beta * x3, c3, fma(r0, x, -target)));
-      double dF = fma(s0 * x, fma(-z, c3, 1.0), fma(beta * x2, c2, r0));
+      const double u1 = fma(-z, c3, 1.0);  // U1 / chi
+      double dF = fma(s0 * x, u1, fma(beta * x2, c2, r0));
+      const double ddF = fma(s0, fma(-z, c2, 1.0), beta * x * u1);
       double dx = F / dF;
       x -= dx;
       it++;
-      if (fabs(dx) <= 1e-14 * fmax(1.0, fabs(x))) done = true;
+      const double tol = fmax(1.0, fabs(x));
+      if (fabs(dx) <= 1e-14 * tol || fabs(ddF) * (dx * dx) <= 2e-15 * tol * fabs(dF)) done = true;
     }
   }
   iters = it;
