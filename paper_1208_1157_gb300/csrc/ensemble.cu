@@ -544,8 +544,8 @@ static int run_plain(swarm_ensemble *e, const StepParams &P) {
       StepParams PG = P;
       PG.t_end_dev = e->d_tend;
       std::vector<double> key = {1.0, (double)b.n, (double)b.S, (double)nmax, P.dt, (double)P.n_corr, P.ce_factor,
-                                 P.eject2, (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)b.x,
-                                 (double)(uintptr_t)W.a0};
+                                 P.eject2, (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)P.log,
+                                 (double)(uintptr_t)b.x, (double)(uintptr_t)W.a0};
       BinView bv = b.view();
       int rc2 = replay_graph(e, key, [&](cudaStream_t cs) -> int {
         for (int k = 1; k <= nmax; k++) CK(launch_plain(bv, PG, W, k, cs));
@@ -614,6 +614,16 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     BinView view;
     int nunits, grid, mapping, variant;
   };
+  // the single-bin kernel of one bin for this integrator (grid 0: only the resident
+  // blocks per SM into *blocks)
+  auto launch_uni = [&](const Uni &u, const StepParams &Q, int g, cudaStream_t st, int *blocks) -> cudaError_t {
+    if (u.mapping == kMapWide)
+      return rkck_family(integrator) ? launch_rkck_wide(u.view, Q, g, st, blocks)
+                                     : launch_hermite_wide(u.view, Q, g, st, blocks);
+    if (hermite_family(integrator)) return launch_hermite_uniform(u.mapping, u.view, u.nunits, Q, g, st, blocks, u.variant);
+    if (rkck_family(integrator)) return launch_rkck_uniform(u.view, u.nunits, Q, g, st, blocks);
+    return launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, Q, g, st, blocks);
+  };
   std::vector<Uni> uni;
   int grid = 0;
   if (per_bin) {
@@ -624,11 +634,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = units_of(u.view.n, u.view.S, u.mapping);
       int blocks = 0;
       u.variant = bin_ctas[i] == 3 ? 1 : 0;
-      if (u.mapping == kMapWide && rkck_family(integrator)) CK(launch_rkck_wide(u.view, P, 0, e->stream, &blocks));
-      else if (u.mapping == kMapWide) CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
-      else if (hermite_family(integrator)) CK(launch_hermite_uniform(u.mapping, u.view, u.nunits, P, 0, e->stream, &blocks, u.variant));
-      else if (rkck_family(integrator)) CK(launch_rkck_uniform(u.view, u.nunits, P, 0, e->stream, &blocks));
-      else CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, P, 0, e->stream, &blocks));
+      CK(launch_uni(u, P, 0, e->stream, &blocks));
       if (blocks <= 0) return fail(SWARM_ECUDA, "single-bin kernel cannot be resident");
       int c = (bin_ctas[i] && bin_ctas[i] < blocks) ? bin_ctas[i] : blocks;
       u.grid = std::max(1, std::min(sms * c, (u.nunits + 3) / 4));
@@ -642,8 +648,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       u.nunits = u.view.S;
       u.variant = 0;
       int blocks = 0;
-      if (rkck_family(integrator)) CK(launch_rkck_wide(u.view, P, 0, e->stream, &blocks));
-      else CK(launch_hermite_wide(u.view, P, 0, e->stream, &blocks));
+      CK(launch_uni(u, P, 0, e->stream, &blocks));
       if (blocks <= 0) return fail(SWARM_ECUDA, "wide kernel cannot be resident");
       u.grid = std::max(1, std::min(sms * blocks, (u.nunits + 3) / 4));
       uni.push_back(u);
@@ -676,18 +681,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       StepParams Qi = Q;
       Qi.work_next = e->d_work_next + 1 + i;
       CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), si));
-      if (uni[i].mapping == kMapWide && rkck_family(integrator))
-        CK(launch_rkck_wide(uni[i].view, Qi, uni[i].grid, si, nullptr));
-      else if (uni[i].mapping == kMapWide)
-        CK(launch_hermite_wide(uni[i].view, Qi, uni[i].grid, si, nullptr));
-      else if (hermite_family(integrator))
-        CK(launch_hermite_uniform(uni[i].mapping, uni[i].view, uni[i].nunits, Qi, uni[i].grid, si, nullptr,
-                                  uni[i].variant));
-      else if (rkck_family(integrator))
-        CK(launch_rkck_uniform(uni[i].view, uni[i].nunits, Qi, uni[i].grid, si, nullptr));
-      else
-        CK(launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, uni[i].view, uni[i].nunits, Qi, uni[i].grid, si,
-                              nullptr));
+      CK(launch_uni(uni[i], Qi, uni[i].grid, si, nullptr));
     }
     for (int j = 0; j < K; j++) {
       CK(cudaEventRecord(e->side_done[j], e->side[j]));
@@ -713,9 +707,10 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   Q.t_end_dev = e->d_tend;
   const double te = P.t_end;
   CK(cudaMemcpyAsync(e->d_tend, &te, sizeof(double), cudaMemcpyHostToDevice, e->stream));
+  // every parameter the captured launches bake in
   std::vector<double> key = {2.0, (double)K, (double)L, (double)integrator, (double)grid, (double)e->nwork, P.dt,
-                             (double)P.n_corr, P.ce_factor, P.eject2, (double)P.log_interval, (double)P.log_cap,
-                             (double)per_bin};
+                             (double)P.n_corr, (double)P.corr_form, P.rk_eps, P.ce_factor, P.eject2,
+                             (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)P.log, (double)per_bin};
   for (int m : maps) key.push_back((double)m);
   for (auto &u : uni) key.push_back((double)u.grid);
   rc = replay_graph(e, key, [&](cudaStream_t cs) -> int {
