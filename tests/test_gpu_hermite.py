@@ -257,3 +257,23 @@ def test_ragged_chunked_launches_with_forked_streams(single):
     assert np.array_equal(got["status"], ref["status"])
     assert np.array_equal(got["time"], ref["time"])
     assert np.array_equal(got["pos"], ref["pos"]) and np.array_equal(got["vel"], ref["vel"])
+
+
+def test_chunked_graph_is_recaptured_when_the_corrector_changes():
+    # same step count per call, corrector switched between calls: the replayed graph must
+    # not keep the first call's corrector
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.three_body(64, seed=21)
+    with S.Ensemble(ens) as e:
+        e.set_option(S.OPT_CORRECTOR, 1)
+        e.integrate(300 * DT, S.HERMITE4, DT)
+        ref = e.state()
+    with S.Ensemble(ens) as e:
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, 50)
+        e.integrate(300 * DT, S.HERMITE4, DT)  # time-symmetric corrector, captured
+        e.set_state(ens["pos"], ens["vel"], time=[0.0] * 64, status=[0] * 64)
+        e.set_option(S.OPT_CORRECTOR, 1)
+        e.integrate(300 * DT, S.HERMITE4, DT)  # same shape of call, printed corrector
+        got = e.state()
+    assert np.array_equal(got["pos"], ref["pos"]) and np.array_equal(got["vel"], ref["vel"])
