@@ -99,7 +99,9 @@ enum swarm_option {
                                     launches run concurrently on forked streams; 1: the bins
                                     with n <= 15 share one persistent launch with a cost-ordered
                                     work list (Hermite and MVS) */
-  SWARM_OPT_CTAS_PER_SM = 7,    /* persistent grid size per SM (0 = tuner/default) */
+  SWARM_OPT_CTAS_PER_SM = 7,    /* persistent grid size per SM (0 = default: the tuner's choice
+                                    for Hermite, full residency for Runge-Kutta, one CTA of 4 warps
+                                    per SM for MVS) */
   SWARM_OPT_CORRECTOR = 8       /* Hermite corrector: 0 = time-symmetric form of Kokubo et al. 1998
                                    (default); 1 = the printed Eq. 4 read with 3/20 and the predicted
                                    base (same velocity update, 4th order, not time-symmetric) */
