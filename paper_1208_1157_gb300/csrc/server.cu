@@ -51,6 +51,7 @@ struct Pool {
   std::vector<int64_t> owner;  // request id per slot, -1 if free
   int32_t *d_list = nullptr;   // occupied slots of the current round (device)
   std::vector<int32_t> h_list;
+  int32_t *h_status = nullptr; // pinned copy of the slots' status after a round
   int *d_next = nullptr;       // work counter of the pool's launch
   int blocks = 0;              // resident CTAs per SM of the pool's kernel
   size_t bytes = 0;
@@ -60,7 +61,10 @@ void free_pool(Pool *q) {
   cudaFree(q->block);
   cudaFree(q->d_list);
   cudaFree(q->d_next);
+  cudaFreeHost(q->h_status);
 }
+
+constexpr int kStageSlots = 1 << 16;  // slot indices one staging batch can carry
 
 constexpr int kSide = 8;  // forked streams for the pools' concurrent launches
 
@@ -127,11 +131,11 @@ struct swarm_server {
   std::deque<int64_t> queue;
   int64_t next_id = 1;
   size_t bytes_used = 0;
-  // staging for one request (caller layout) and its slot list
-  double *d_stage = nullptr;
-  int *d_slots = nullptr;
+  // staging for a batch of requests (caller layout) and their slot lists: device buffers
+  // and pinned host mirrors, so that a batch moves in one copy each way
+  double *d_stage = nullptr, *h_stage = nullptr;
+  int *d_slots = nullptr, *h_slots = nullptr;
   size_t stage_doubles = 0;
-  std::vector<int32_t> h_status;
   // concurrent launches of the pools: side streams forked from and joined to `stream`
   cudaStream_t side[kSide] = {};
   cudaEvent_t side_done[kSide] = {};
@@ -197,6 +201,7 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
   p->owner.assign(cap, -1);
   SCK(cudaMalloc(&p->d_list, sizeof(int32_t) * cap));
   SCK(cudaMalloc(&p->d_next, sizeof(int)));
+  SCK(cudaMallocHost(&p->h_status, sizeof(int32_t) * cap));
   p->h_list.reserve(cap);
   // body-per-lane kernels that take the slot list and hand slots out per group
   StepParams Q{};
@@ -222,7 +227,9 @@ extern "C" int swarm_server_create(const swarm_server_config *cfg, void *cuda_st
   sv->stream = (cudaStream_t)cuda_stream;
   sv->stage_doubles = (size_t)4096 * SWARM_RING_MAX_N * 7 + 4096 * 2;
   SCK(cudaMalloc(&sv->d_stage, sizeof(double) * sv->stage_doubles));
-  SCK(cudaMalloc(&sv->d_slots, sizeof(int) * 4096));
+  SCK(cudaMallocHost(&sv->h_stage, sizeof(double) * sv->stage_doubles));
+  SCK(cudaMalloc(&sv->d_slots, sizeof(int) * kStageSlots));
+  SCK(cudaMallocHost(&sv->h_slots, sizeof(int) * kStageSlots));
   SCK(cudaMalloc(&sv->d_counters, sizeof(unsigned long long) * 4));
   SCK(cudaEventCreate(&sv->ev0));
   SCK(cudaEventCreate(&sv->ev1));
@@ -247,6 +254,8 @@ extern "C" void swarm_server_destroy(swarm_server *sv) {
   if (sv->fork_ev) cudaEventDestroy(sv->fork_ev);
   cudaFree(sv->d_stage);
   cudaFree(sv->d_slots);
+  cudaFreeHost(sv->h_stage);
+  cudaFreeHost(sv->h_slots);
   cudaFree(sv->d_counters);
   cudaEventDestroy(sv->ev0);
   cudaEventDestroy(sv->ev1);
@@ -285,7 +294,34 @@ extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_bo
   return SWARM_OK;
 }
 
+// Admission in batches: every queued request that fits into its pool gets slots, its
+// arrays are packed into the pinned staging buffer, and each full batch moves to the
+// device in one copy per array followed by one scatter kernel per request.
 static int admit(swarm_server *sv) {
+  struct Item {
+    Request *r;
+    size_t d_off, s_off;
+  };
+  std::vector<Item> batch;
+  size_t d_used = 0, s_used = 0;
+  auto flush = [&]() -> int {
+    if (batch.empty()) return SWARM_OK;
+    SCK(cudaMemcpyAsync(sv->d_stage, sv->h_stage, sizeof(double) * d_used, cudaMemcpyHostToDevice, sv->stream));
+    SCK(cudaMemcpyAsync(sv->d_slots, sv->h_slots, sizeof(int) * s_used, cudaMemcpyHostToDevice, sv->stream));
+    for (auto &it : batch) {
+      Request *r = it.r;
+      const size_t nb = (size_t)r->n_sys * r->n;
+      const double *dpos = sv->d_stage + it.d_off, *dvel = dpos + 3 * nb, *dmass = dvel + 3 * nb;
+      admit_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(r->pool->view, r->pool->t_end,
+                                                                    sv->d_slots + it.s_off, r->n_sys, dpos, dvel,
+                                                                    dmass, r->t0, r->t_end);
+      SCK(cudaGetLastError());
+    }
+    SCK(cudaStreamSynchronize(sv->stream));  // the staging buffers are reused by the next batch
+    batch.clear();
+    d_used = s_used = 0;
+    return SWARM_OK;
+  };
   for (auto it = sv->queue.begin(); it != sv->queue.end();) {
     Request *r = sv->reqs[*it].get();
     Pool *p = nullptr;
@@ -295,6 +331,9 @@ static int admit(swarm_server *sv) {
       ++it;
       continue;
     }
+    const size_t nb = (size_t)r->n_sys * r->n;
+    if (d_used + 7 * nb > sv->stage_doubles || s_used + r->n_sys > (size_t)kStageSlots)
+      if ((rc = flush())) return rc;
     r->slots.resize(r->n_sys);
     for (int i = 0; i < r->n_sys; i++) {
       const int slot = *p->free_slots.begin();
@@ -303,77 +342,103 @@ static int admit(swarm_server *sv) {
       p->owner[slot] = r->id;
     }
     r->pool = p;
-    const size_t nb = (size_t)r->n_sys * r->n;
-    double *dpos = sv->d_stage, *dvel = dpos + 3 * nb, *dmass = dvel + 3 * nb;
-    SCK(cudaMemcpyAsync(dpos, r->pos.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, sv->stream));
-    SCK(cudaMemcpyAsync(dvel, r->vel.data(), sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, sv->stream));
-    SCK(cudaMemcpyAsync(dmass, r->mass.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, sv->stream));
-    SCK(cudaMemcpyAsync(sv->d_slots, r->slots.data(), sizeof(int) * r->n_sys, cudaMemcpyHostToDevice, sv->stream));
-    admit_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(p->view, p->t_end, sv->d_slots, r->n_sys, dpos, dvel,
-                                                                  dmass, r->t0, r->t_end);
-    SCK(cudaGetLastError());
-    SCK(cudaStreamSynchronize(sv->stream));  // staging is reused by the next admission
+    double *h = sv->h_stage + d_used;
+    std::memcpy(h, r->pos.data(), sizeof(double) * 3 * nb);
+    std::memcpy(h + 3 * nb, r->vel.data(), sizeof(double) * 3 * nb);
+    std::memcpy(h + 6 * nb, r->mass.data(), sizeof(double) * nb);
+    std::memcpy(sv->h_slots + s_used, r->slots.data(), sizeof(int) * r->n_sys);
+    batch.push_back(Item{r, d_used, s_used});
+    d_used += 7 * nb;
+    s_used += r->n_sys;
     r->state = SWARM_REQ_RUNNING;
     r->pos.clear();
     r->vel.clear();
     sv->stats.admitted++;
     it = sv->queue.erase(it);
   }
-  return SWARM_OK;
+  return flush();
 }
 
+// Retirement: the statuses of every occupied pool come back in one round of copies; the
+// requests whose systems all reached t_end or stopped are gathered in batches (one
+// gather kernel per request, one copy of the batch to the pinned staging buffer) and
+// their slots freed.
 static int retire(swarm_server *sv, int32_t *n_completed) {
-  // which requests are complete: every slot DONE or stopped
-  std::map<int64_t, int> pending;  // request id -> slots not finished
+  std::vector<Pool *> occ;
   for (auto &kv : sv->pools) {
     Pool *p = kv.second.get();
-    bool any = false;
-    for (int64_t o : p->owner)
-      if (o >= 0) {
-        any = true;
-        break;
-      }
-    if (!any) continue;
-    sv->h_status.resize(p->cap);
-    SCK(cudaMemcpyAsync(sv->h_status.data(), p->view.status, sizeof(int32_t) * p->cap, cudaMemcpyDeviceToHost, sv->stream));
-    SCK(cudaStreamSynchronize(sv->stream));
+    if ((int)p->free_slots.size() == p->cap) continue;
+    SCK(cudaMemcpyAsync(p->h_status, p->view.status, sizeof(int32_t) * p->cap, cudaMemcpyDeviceToHost, sv->stream));
+    occ.push_back(p);
+  }
+  if (occ.empty()) return SWARM_OK;
+  SCK(cudaStreamSynchronize(sv->stream));
+  std::map<int64_t, int> pending;  // request id -> slots not finished
+  for (Pool *p : occ)
     for (int s = 0; s < p->cap; s++) {
-      int64_t o = p->owner[s];
+      const int64_t o = p->owner[s];
       if (o < 0) continue;
       int &c = pending[o];
-      if (sv->h_status[s] == SWARM_SYS_ACTIVE) c++;
+      if (p->h_status[s] == SWARM_SYS_ACTIVE) c++;
     }
-  }
+  struct Item {
+    Request *r;
+    size_t d_off, s_off;
+  };
+  std::vector<Item> batch;
+  size_t d_used = 0, s_used = 0;
+  auto flush = [&]() -> int {
+    if (batch.empty()) return SWARM_OK;
+    SCK(cudaMemcpyAsync(sv->d_slots, sv->h_slots, sizeof(int) * s_used, cudaMemcpyHostToDevice, sv->stream));
+    for (auto &it : batch) {
+      Request *r = it.r;
+      const size_t nb = (size_t)r->n_sys * r->n;
+      double *dpos = sv->d_stage + it.d_off, *dvel = dpos + 3 * nb, *dtime = dvel + 3 * nb;
+      int32_t *dstat = (int32_t *)(dtime + r->n_sys);
+      retire_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(r->pool->view, sv->d_slots + it.s_off, r->n_sys,
+                                                                     dpos, dvel, dtime, dstat);
+      SCK(cudaGetLastError());
+    }
+    SCK(cudaMemcpyAsync(sv->h_stage, sv->d_stage, sizeof(double) * d_used, cudaMemcpyDeviceToHost, sv->stream));
+    SCK(cudaStreamSynchronize(sv->stream));
+    for (auto &it : batch) {
+      Request *r = it.r;
+      const size_t nb = (size_t)r->n_sys * r->n;
+      const double *h = sv->h_stage + it.d_off;
+      r->out_pos.assign(h, h + 3 * nb);
+      r->out_vel.assign(h + 3 * nb, h + 6 * nb);
+      r->out_time.assign(h + 6 * nb, h + 6 * nb + r->n_sys);
+      const int32_t *hs = (const int32_t *)(h + 6 * nb + r->n_sys);
+      r->out_status.assign(hs, hs + r->n_sys);
+      for (int sl : r->slots) {
+        r->pool->owner[sl] = -1;
+        r->pool->free_slots.insert(sl);
+      }
+      r->slots.clear();
+      r->state = SWARM_REQ_DONE;
+      r->finished = Clock::now();
+      sv->stats.completed++;
+      (*n_completed)++;
+    }
+    batch.clear();
+    d_used = s_used = 0;
+    return SWARM_OK;
+  };
   for (auto &kv : pending) {
     if (kv.second) continue;
     Request *r = sv->reqs[kv.first].get();
-    Pool *p = r->pool;
     const size_t nb = (size_t)r->n_sys * r->n;
-    double *dpos = sv->d_stage, *dvel = dpos + 3 * nb, *dtime = dvel + 3 * nb;
-    int32_t *dstat = (int32_t *)(dtime + r->n_sys);
-    SCK(cudaMemcpyAsync(sv->d_slots, r->slots.data(), sizeof(int) * r->n_sys, cudaMemcpyHostToDevice, sv->stream));
-    retire_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(p->view, sv->d_slots, r->n_sys, dpos, dvel, dtime, dstat);
-    SCK(cudaGetLastError());
-    r->out_pos.resize(3 * nb);
-    r->out_vel.resize(3 * nb);
-    r->out_time.resize(r->n_sys);
-    r->out_status.resize(r->n_sys);
-    SCK(cudaMemcpyAsync(r->out_pos.data(), dpos, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, sv->stream));
-    SCK(cudaMemcpyAsync(r->out_vel.data(), dvel, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, sv->stream));
-    SCK(cudaMemcpyAsync(r->out_time.data(), dtime, sizeof(double) * r->n_sys, cudaMemcpyDeviceToHost, sv->stream));
-    SCK(cudaMemcpyAsync(r->out_status.data(), dstat, sizeof(int32_t) * r->n_sys, cudaMemcpyDeviceToHost, sv->stream));
-    SCK(cudaStreamSynchronize(sv->stream));
-    for (int s : r->slots) {
-      p->owner[s] = -1;
-      p->free_slots.insert(s);
-    }
-    r->slots.clear();
-    r->state = SWARM_REQ_DONE;
-    r->finished = Clock::now();
-    sv->stats.completed++;
-    (*n_completed)++;
+    // pos, vel (3 nb each), time (n_sys), status (n_sys int32 in n_sys/2 + 1 doubles)
+    const size_t need = 6 * nb + r->n_sys + (r->n_sys + 1) / 2 + 1;
+    int rc;
+    if (d_used + need > sv->stage_doubles || s_used + r->n_sys > (size_t)kStageSlots)
+      if ((rc = flush())) return rc;
+    std::memcpy(sv->h_slots + s_used, r->slots.data(), sizeof(int) * r->n_sys);
+    batch.push_back(Item{r, d_used, s_used});
+    d_used += need;
+    s_used += r->n_sys;
   }
-  return SWARM_OK;
+  return flush();
 }
 
 extern "C" int swarm_server_step(swarm_server *sv, int32_t *n_completed) {
