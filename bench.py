@@ -306,8 +306,10 @@ def secondary(S, torch, stream):
     out["c3_ragged_hermite_single_launch_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT, single=1)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
+    out["c4_mvs_jacobi_2000_steps_2cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=2)
     out["c4_mvs_jacobi_2000_steps_3cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=3)
     out["c4_mvs_jacobi_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, outcome=True)
+    out["c4_mvs_jacobi_1e5_steps_2cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=2)
     out["c4_mvs_jacobi_1e5_steps_3cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=3)
     out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)
     out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
