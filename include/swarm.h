@@ -120,9 +120,8 @@ typedef struct {
 
 /* ------------------------------------------------------------------ ensembles */
 /* Create an ensemble of n_sys systems and upload its initial state (host arrays).
- * n_body[s] in 2..32 (systems of more than 15 bodies are integrated by the Hermite and
- * Runge-Kutta integrators only: one system per warp); mass > 0 and finite; pos/vel
- * finite; time of every system t0.
+ * n_body[s] in 2..32 (systems of 16..32 bodies run one system per warp); mass > 0 and
+ * finite; pos/vel finite; time of every system t0.
  * cuda_stream: a cudaStream_t to run on (NULL = the legacy default stream).
  * Returns SWARM_EINVAL for bad sizes/values, SWARM_ENOMEM, SWARM_ECUDA. */
 int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const double *mass, const double *pos,

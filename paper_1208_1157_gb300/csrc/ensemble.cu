@@ -617,9 +617,11 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   // the single-bin kernel of one bin for this integrator (grid 0: only the resident
   // blocks per SM into *blocks)
   auto launch_uni = [&](const Uni &u, const StepParams &Q, int g, cudaStream_t st, int *blocks) -> cudaError_t {
-    if (u.mapping == kMapWide)
-      return rkck_family(integrator) ? launch_rkck_wide(u.view, Q, g, st, blocks)
-                                     : launch_hermite_wide(u.view, Q, g, st, blocks);
+    if (u.mapping == kMapWide) {
+      if (rkck_family(integrator)) return launch_rkck_wide(u.view, Q, g, st, blocks);
+      if (hermite_family(integrator)) return launch_hermite_wide(u.view, Q, g, st, blocks);
+      return launch_mvs_wide(u.view, Q, g, st, blocks);
+    }
     if (hermite_family(integrator)) return launch_hermite_uniform(u.mapping, u.view, u.nunits, Q, g, st, blocks, u.variant);
     if (rkck_family(integrator)) return launch_rkck_uniform(u.view, u.nunits, Q, g, st, blocks);
     return launch_mvs_uniform(integrator == SWARM_MVS_JACOBI, u.view, u.nunits, Q, g, st, blocks);
@@ -734,11 +736,6 @@ static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, doubl
   if (!adaptive(integrator) && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
   if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && (integrator != SWARM_HERMITE4 || e->corr_form))
     return fail(SWARM_EINVAL, "the plain per-step baseline exists for the fixed-step time-symmetric Hermite only");
-  if (!hermite_family(integrator) && !rkck_family(integrator))
-    for (auto &b : e->bins)
-      if (b.n > SWARM_RING_MAX_N)
-        return fail(SWARM_EINVAL, "systems of more than %d bodies are integrated by the Hermite and Runge-Kutta "
-                    "integrators only", SWARM_RING_MAX_N);
   StepParams P = make_params(e, t_end, integrator, dt);
   CK(cudaMemsetAsync(e->d_counters, 0, sizeof(unsigned long long) * 4, e->stream));
   e->launches = 0;

@@ -53,6 +53,8 @@ inline cudaError_t launch_rkck_uniform(const BinView &B, int nunits, const StepP
 
 // Hermite for 16..32-body bins: one system per warp (work unit = system).
 cudaError_t launch_hermite_wide(const BinView &B, const StepParams &P, int grid, cudaStream_t st, int *blocks);
+// MVS for 16..32-body bins: one system per warp.
+cudaError_t launch_mvs_wide(const BinView &B, const StepParams &P, int grid, cudaStream_t st, int *blocks);
 // Runge-Kutta Cash-Karp for 16..32-body bins: one system per warp.
 cudaError_t launch_rkck_wide(const BinView &B, const StepParams &P, int grid, cudaStream_t st, int *blocks);
 

@@ -74,12 +74,23 @@ def test_wide_logs_and_chunked_launches():
     assert ex.max() == 0.0 and ev.max() == 0.0
 
 
-def test_wide_systems_refuse_mvs():
-    from paper_1208_1157_gb300 import swarm as S
-    with S.Ensemble(ics.ragged_wide(4, seed=36)) as e:
-        for integ in (S.MVS_DH, S.MVS_JACOBI):
-            with pytest.raises(S.SwarmError):
-                e.integrate(0.1, integ, 0.01)
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_wide_mvs_parity(kind):
+    # 16..32-body systems next to smaller ones, dt = 1/20 inner period, shortened last
+    # step, stops on (2 mutual Hill radii: the stops spread over the call), logs every 50
+    # steps
+    ens = ics.concat(ics.ragged_wide(48, seed=36), ics.ragged(40, seed=39, n_max=8))
+    dt = TWO_PI / 20
+    t_end = 300.5 * dt
+    o = run_oracle(ens, t_end, kind, dt, ce=2.0, ej=100.0, log_interval=50, log_cap=8)
+    sens = oracle_sensitivity(ens, t_end, kind, dt, ce=2.0, ej=100.0)
+    g = run_gpu(ens, t_end, kind, dt, ce=2.0, ej=100.0, log_interval=50, log_cap=8)
+    assert_parity(ens, g, o, sens=sens, steps=301)
+    for s in range(len(ens["n_body"])):
+        lg = g["logs"][s]
+        assert len(lg) == o["log_count"][s]
+        if len(lg):
+            np.testing.assert_allclose(lg[:, 0], o["log"][s, :len(lg), 0], rtol=1e-14)
 
 
 def test_wide_runge_kutta_parity():
