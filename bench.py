@@ -319,6 +319,8 @@ def secondary(S, torch, stream):
     out["c3_ragged_rkck_100_steps"] = timed(c3, 100 * DT, S.RKCK, DT)
     c6 = ics.ragged_wide(16384, seed=6)
     out["wide_16_to_32_bodies_hermite_20_steps"] = timed(c6, 20 * DT, S.HERMITE4, DT)
+    out["wide_16_to_32_bodies_mvs_jacobi_100_steps"] = timed(c6, 100 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
+    out["wide_16_to_32_bodies_rkck_20_steps"] = timed(c6, 20 * DT, S.RKCK, DT)
     out["serving"] = serving(S, stream)
     return out
 
