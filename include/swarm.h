@@ -159,6 +159,14 @@ int swarm_query_state(const swarm_ensemble *ens, double *pos, double *vel, doubl
 /* Same into caller-owned device arrays, enqueued on the ensemble's stream (no wait). */
 int swarm_query_state_dev(const swarm_ensemble *ens, double *d_pos, double *d_vel, double *d_time,
                           int32_t *d_status);
+/* Replace the state from caller-owned device arrays in the creation layout (any pointer
+ * may be NULL to keep that part), enqueued on the ensemble's stream; the arrays must stay
+ * valid until the stream reaches the copy.  Values are not checked on the host, except
+ * the times, which are read back (one copy and a wait) to bound later step counts
+ * (SWARM_EINVAL if one is not finite).  Status values must be 0..5; a non-finite
+ * position or velocity stops its system at its first step (NONFINITE). */
+int swarm_set_state_dev(swarm_ensemble *ens, const double *d_pos, const double *d_vel, const double *d_time,
+                        const int32_t *d_status);
 /* Energy (Eq. 6, each pair once) and angular momentum [n_sys][3] of the current state,
  * computed on the device; host arrays. */
 int swarm_query_diagnostics(const swarm_ensemble *ens, double *energy, double *angmom);

@@ -795,6 +795,26 @@ static int pack_to(const swarm_ensemble *e, double *pos, double *vel, double *ti
   return SWARM_OK;
 }
 
+extern "C" int swarm_set_state_dev(swarm_ensemble *e, const double *d_pos, const double *d_vel, const double *d_time,
+                                   const int32_t *d_status) {
+  if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");
+  cudaStream_t st = e->stream;
+  if (d_time) {  // the step-count guard needs the range of the new times on the host
+    std::vector<double> h(e->n_sys);
+    CK(cudaMemcpyAsync(h.data(), d_time, sizeof(double) * e->n_sys, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int rc = check_finite(h.data(), e->n_sys, "time");
+    if (rc) return rc;
+    e->t_lo = *std::min_element(h.begin(), h.end());
+    e->t_hi = *std::max_element(h.begin(), h.end());
+  }
+  for (auto &b : e->bins) {
+    unpack_kernel<<<(b.S + 127) / 128, 128, 0, st>>>(b.view(), e->d_offs, d_pos, d_vel, nullptr, d_time, d_status);
+    CK(cudaGetLastError());
+  }
+  return SWARM_OK;
+}
+
 extern "C" int swarm_query_state_dev(const swarm_ensemble *e, double *d_pos, double *d_vel, double *d_time,
                                      int32_t *d_status) {
   if (!e) return fail(SWARM_EINVAL, "ensemble is NULL");

@@ -25,7 +25,7 @@ OPT_MAPPING, OPT_N_CORR, OPT_LOG_INTERVAL, OPT_LOG_CAPACITY, OPT_STEPS_PER_LAUNC
 EXPORTS = (
     "swarm_create_ensemble", "swarm_set_stop", "swarm_set_option", "swarm_set_tolerance", "swarm_query_rv",
     "swarm_observe_rv", "swarm_integrate", "swarm_integrate_async",
-    "swarm_synchronize", "swarm_set_state", "swarm_query_state", "swarm_query_state_dev", "swarm_query_diagnostics",
+    "swarm_synchronize", "swarm_set_state", "swarm_query_state", "swarm_query_state_dev", "swarm_set_state_dev", "swarm_query_diagnostics",
     "swarm_query_log", "swarm_query_stats", "swarm_ensemble_size", "swarm_destroy_ensemble", "swarm_tuner_choice",
     "swarm_tuner_load", "swarm_tuner_save", "swarm_fp64_peak", "swarm_last_error", "swarm_version",
     "swarm_hermite_integrate_noalloc",
@@ -71,6 +71,7 @@ def lib():
             L.swarm_set_state.argtypes = [_vp, _dp, _dp, _dp, _ip]
             L.swarm_query_state.argtypes = [_vp, _dp, _dp, _dp, _ip]
             L.swarm_query_state_dev.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            L.swarm_set_state_dev.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.swarm_query_diagnostics.argtypes = [_vp, _dp, _dp]
             L.swarm_query_log.argtypes = [_vp, C.c_int32, _dp, C.c_int32, _ip]
             L.swarm_query_stats.argtypes = [_vp, C.POINTER(Stats)]
@@ -179,6 +180,12 @@ class Ensemble:
         """Host-pointer variant writing into caller-owned (e.g. pinned) numpy arrays."""
         _check(lib().swarm_query_state(self._h, _d(pos), _d(vel), _d(time),
                                        None if status is None else status.ctypes.data_as(_ip)))
+
+    def set_state_dev(self, pos_t=None, vel_t=None, time_t=None, status_t=None):
+        """Replace the state from device tensors (float64 [B,3], [B,3], [S]; int32 [S]),
+        enqueued on the ensemble's stream."""
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(lib().swarm_set_state_dev(self._h, ptr(pos_t), ptr(vel_t), ptr(time_t), ptr(status_t)))
 
     def state_dev(self, pos_t=None, vel_t=None, time_t=None, status_t=None):
         """Write the state into caller-owned torch CUDA tensors (float64 / int32), on the stream."""

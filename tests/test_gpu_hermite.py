@@ -277,3 +277,30 @@ def test_chunked_graph_is_recaptured_when_the_corrector_changes():
         e.integrate(300 * DT, S.HERMITE4, DT)  # same shape of call, printed corrector
         got = e.state()
     assert np.array_equal(got["pos"], ref["pos"]) and np.array_equal(got["vel"], ref["vel"])
+
+
+def test_device_pointer_state_round_trip():
+    # state in and out through device arrays (torch tensors on the ensemble's stream)
+    import torch
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.ragged(200, seed=22)
+    ref = run_gpu(ens, 100 * DT, 1, DT)
+    nb, ns = int(np.sum(ens["n_body"])), len(ens["n_body"])
+    stream = torch.cuda.current_stream()
+    with S.Ensemble(ens, stream=stream) as e:
+        e.integrate(37 * DT, S.HERMITE4, DT)  # move away from the initial state
+        pos_t = torch.tensor(ens["pos"], dtype=torch.float64, device="cuda")
+        vel_t = torch.tensor(ens["vel"], dtype=torch.float64, device="cuda")
+        time_t = torch.zeros(ns, dtype=torch.float64, device="cuda")
+        st_t = torch.zeros(ns, dtype=torch.int32, device="cuda")
+        e.set_state_dev(pos_t, vel_t, time_t, st_t)
+        e.integrate(100 * DT, S.HERMITE4, DT)
+        out_p = torch.empty((nb, 3), dtype=torch.float64, device="cuda")
+        out_v = torch.empty((nb, 3), dtype=torch.float64, device="cuda")
+        out_t = torch.empty(ns, dtype=torch.float64, device="cuda")
+        out_s = torch.empty(ns, dtype=torch.int32, device="cuda")
+        e.state_dev(out_p, out_v, out_t, out_s)
+        stream.synchronize()
+    assert np.array_equal(out_p.cpu().numpy(), ref["pos"]) and np.array_equal(out_v.cpu().numpy(), ref["vel"])
+    assert np.array_equal(out_t.cpu().numpy(), ref["time"]) and np.array_equal(out_s.cpu().numpy(), ref["status"])
