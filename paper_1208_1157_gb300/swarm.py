@@ -225,6 +225,26 @@ class Ensemble:
         return {f: getattr(s, f) for f, _ in Stats._fields_}
 
 
+def save_checkpoint(e: "Ensemble", path: str) -> None:
+    """Write the ensemble's current state (masses, positions, velocities, times and
+    statuses) to an .npz file; `load_checkpoint` + `Ensemble.resume` continue from it."""
+    st = e.state()
+    np.savez(path, n_body=e.n_body, mass=e._mass, pos=st["pos"], vel=st["vel"], time=st["time"], status=st["status"])
+
+
+def load_checkpoint(path: str) -> dict:
+    """Read a checkpoint written by `save_checkpoint` (the ics layout plus time, status)."""
+    with np.load(path) as f:
+        return {k: f[k] for k in ("n_body", "mass", "pos", "vel", "time", "status")}
+
+
+def resume(ckpt: dict, stream=None) -> "Ensemble":
+    """A new ensemble holding a checkpoint's state, times and statuses."""
+    e = Ensemble(ckpt, stream=stream)
+    e.set_state(time=ckpt["time"], status=ckpt["status"])
+    return e
+
+
 def fp64_peak(seconds=0.3, stream=None) -> float:
     out = C.c_double()
     _check(lib().swarm_fp64_peak(float(seconds), _stream_ptr(stream), C.byref(out)))

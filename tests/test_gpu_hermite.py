@@ -304,3 +304,22 @@ def test_device_pointer_state_round_trip():
         stream.synchronize()
     assert np.array_equal(out_p.cpu().numpy(), ref["pos"]) and np.array_equal(out_v.cpu().numpy(), ref["vel"])
     assert np.array_equal(out_t.cpu().numpy(), ref["time"]) and np.array_equal(out_s.cpu().numpy(), ref["status"])
+
+
+def test_checkpoint_and_resume(tmp_path):
+    # stop half way, write the state to disk, resume in a new ensemble: the same result
+    # as one call, bit for bit (a0, j0 are recomputed from the stored state)
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.ragged(150, seed=23)
+    ref = run_gpu(ens, 400 * DT, 1, DT, ce=3.0, ej=100.0)
+    with S.Ensemble(ens) as e:
+        e.set_stop(3.0, 100.0)
+        e.integrate(150 * DT, S.HERMITE4, DT)
+        S.save_checkpoint(e, str(tmp_path / "ck.npz"))
+    with S.resume(S.load_checkpoint(str(tmp_path / "ck.npz"))) as e:
+        e.set_stop(3.0, 100.0)
+        e.integrate(400 * DT, S.HERMITE4, DT)
+        got = e.state()
+    for k in ("pos", "vel", "time", "status"):
+        assert np.array_equal(got[k], ref[k]), k
