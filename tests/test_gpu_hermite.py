@@ -139,17 +139,21 @@ def test_paper_shaped_ensemble_full_size_sampled():
     assert g["stats"]["system_steps"] > 0.99 * 131072 * 10000
 
 
-def test_ragged_full_size_sampled():
+@pytest.mark.parametrize("single", [0, 1])
+def test_ragged_full_size_sampled(single):
+    # the 65536-system ragged ensemble as the benchmark runs it (100 steps, stops on), in
+    # concurrent per-bin launches (the default) and in the shared launch; 40 samples
     ens = ics.ragged(65536, seed=3)
-    g = run_gpu(ens, 10 * DT, 1, DT, mapping=0)
+    g = run_gpu(ens, 100 * DT, 1, DT, mapping=0, ce=3.0, ej=100.0, single_launch=single)
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(65536, 40, replace=False))
     sub = ics.subset(ens, idx)
-    o = run_oracle(sub, 10 * DT, O.HERMITE, DT)
+    o = run_oracle(sub, 100 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(sub, 100 * DT, O.HERMITE, DT, ce=3.0, ej=100.0)
     offs = np.concatenate([[0], np.cumsum(ens["n_body"])])
     rows = np.concatenate([np.arange(offs[s], offs[s + 1]) for s in idx])
     gs = {"pos": g["pos"][rows], "vel": g["vel"][rows], "time": g["time"][idx], "status": g["status"][idx]}
-    assert_parity(sub, gs, o)
+    assert_parity(sub, gs, o, sens=sens, steps=100)
 
 
 @pytest.mark.parametrize("mapping", [0, 3])
