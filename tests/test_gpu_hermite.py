@@ -311,7 +311,7 @@ def test_device_pointer_state_round_trip():
 
 
 def test_checkpoint_and_resume(tmp_path):
-    # stop half way, write the state to disk, resume in a new ensemble: the same result
+    # stop half way, write the state to disk, resume in a new ensemble: the same states
     # as one call, bit for bit (a0, j0 are recomputed from the stored state)
     from paper_1208_1157_gb300 import swarm as S
 
@@ -325,5 +325,8 @@ def test_checkpoint_and_resume(tmp_path):
         e.set_stop(3.0, 100.0)
         e.integrate(400 * DT, S.HERMITE4, DT)
         got = e.state()
-    for k in ("pos", "vel", "time", "status"):
+    for k in ("pos", "vel", "status"):
         assert np.array_equal(got[k], ref[k]), k
+    # times are t0 + k dt from each call's start, so a stop time after the resume can
+    # differ from the one-call value in the last place
+    np.testing.assert_allclose(got["time"], ref["time"], rtol=1e-15, atol=0)
