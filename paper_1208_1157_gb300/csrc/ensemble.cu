@@ -98,6 +98,9 @@ struct swarm_ensemble {
   std::vector<cudaEvent_t> side_done;
   cudaEvent_t fork_ev = nullptr;
   double *d_tend = nullptr;
+  // longest-first system lists of the bins for the adaptive integrators
+  int32_t *d_order = nullptr;
+  int *d_order_scratch = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
   swarm_stats stats{};
@@ -208,6 +211,8 @@ static void free_all(swarm_ensemble *e) {
   for (auto st : e->side) cudaStreamDestroy(st);
   for (auto ev : e->side_done) cudaEventDestroy(ev);
   if (e->fork_ev) cudaEventDestroy(e->fork_ev);
+  if (e->d_order) cudaFree(e->d_order);
+  if (e->d_order_scratch) cudaFree(e->d_order_scratch);
 }
 
 constexpr int kSideStreams = 8;
@@ -659,6 +664,25 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     if (maxb <= 0) return fail(SWARM_ECUDA, "persistent kernel cannot be resident");
     if (!ctas || ctas > maxb) ctas = maxb;
     grid = std::max(1, std::min(sms * ctas, (e->nwork + 3) / 4));
+  }
+  // Adaptive integrators: the single-bin launches hand their systems out longest first
+  // (expected step count from Eq. 5 at the current state), so that the calls do not end
+  // with a few long integrations running alone.
+  if (adaptive(integrator) && !uni.empty()) {
+    if (!e->d_order) {
+      size_t scratch = 0;
+      for (auto &b : e->bins) scratch = std::max(scratch, order_scratch_ints(b.S));
+      CK(cudaMalloc(&e->d_order, sizeof(int32_t) * (size_t)e->n_sys));
+      CK(cudaMalloc(&e->d_order_scratch, sizeof(int) * scratch));
+    }
+    size_t off = 0;
+    for (auto &u : uni) {
+      CK(order_longest_first(u.view, P.t_end, e->d_order + off, e->d_order_scratch, e->stream));
+      u.view.list = e->d_order + off;
+      u.view.nlist = u.view.S;
+      off += (size_t)u.view.S;
+      e->launches += 3;
+    }
   }
   // With more than one launch per round, the single-bin launches run on side streams
   // forked from the main stream (heaviest bin first), so that one launch's tail overlaps

@@ -58,6 +58,11 @@ cudaError_t launch_mvs_wide(const BinView &B, const StepParams &P, int grid, cud
 // Runge-Kutta Cash-Karp for 16..32-body bins: one system per warp.
 cudaError_t launch_rkck_wide(const BinView &B, const StepParams &P, int grid, cudaStream_t st, int *blocks);
 
+// Longest-first system list of a bin for the adaptive integrators (order.cu): list[S],
+// scratch of order_scratch_ints(S) ints.
+size_t order_scratch_ints(int S);
+cudaError_t order_longest_first(const BinView &B, double t_end, int32_t *list, int *scratch, cudaStream_t st);
+
 void set_last_error(const char *msg);
 
 cudaError_t launch_fp64_peak(double *out, long long iters, int grid, int block, cudaStream_t st);
