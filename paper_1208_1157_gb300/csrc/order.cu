@@ -4,10 +4,11 @@
 // reach t_end, and a launch that hands systems out in index order ends with a few long
 // integrations running alone on a mostly idle GPU.  Before such a launch each system's
 // expected step count, |t_end - t| times the Eq. 5 rate (sum_i |j_i|^2 / |a_i|^2)^(1/2)
-// at its current state, is put into a quarter-octave class, and a counting sort lists
+// at its current state, is put into an eighth-of-an-octave class, and a counting sort lists
 // the systems from the most expensive class down; the kernels hand the list out in that
-// order (longest processing time first).  The order inside a class is whatever the
-// atomics give: each system's arithmetic does not depend on where it runs.
+// order (longest processing time first), so that the systems a warp takes together
+// need similar step counts.  The order inside a class is whatever the atomics give: each
+// system's arithmetic does not depend on where it runs.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -58,7 +59,7 @@ __global__ void order_cost_kernel(BinView B, double t_end, int *__restrict__ cls
     }
     const double te = B.t_end ? B.t_end[s] : t_end;
     const double steps = fabs(te - B.t[s]) * sqrt(sum);
-    if (steps > 0.0 && !nonfinite(steps)) c = min(kClasses - 1, max(0, (int)(4.0 * log2(1.0 + steps))));
+    if (steps > 0.0 && !nonfinite(steps)) c = min(kClasses - 1, max(0, (int)(8.0 * log2(1.0 + steps))));
   }
   cls[s] = c;
   atomicAdd(&hist[c], 1);
