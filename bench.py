@@ -313,6 +313,7 @@ def secondary(S, torch, stream):
     out["c4_mvs_jacobi_1e5_steps_3cta"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=3)
     out["c4_mvs_dh_1e5_steps"] = timed(c4, 1e5 * TWO_PI / 20, S.MVS_DH, TWO_PI / 20, outcome=True)
     out["c2_hermite_adaptive_tau_0.01_one_period"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01)
+    out["c2_hermite_adaptive_tau_0.01_one_period_2cta"] = timed(c2, TWO_PI, S.HERMITE4_ADAPTIVE, 0.01, ctas=2)
     out["c2_rkck_fixed_500"] = timed(c2, 500 * DT, S.RKCK, DT)
     out["c2_rkck_fixed_1cta_500"] = timed(c2, 500 * DT, S.RKCK, DT, ctas=1)
     out["c2_rkck_adaptive_eps_1e-12_one_period"] = timed(c2, TWO_PI, S.RKCK_ADAPTIVE, 0.05)

@@ -605,6 +605,10 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     // halves the step time of the last systems of a call (16384 x 8 compact ensemble:
     // +4 % over 2000 steps, +35 % over 1e5 steps, where few systems run the last steps)
     if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) bin_ctas[i] = 1;
+    // adaptive system per lane: each lane integrates systems one after the other, so the
+    // call ends with lanes waiting for the last ones; one CTA per SM gives every lane
+    // more systems and makes that tail a smaller part of the call
+    if (integrator == SWARM_HERMITE4_ADAPTIVE && m == SWARM_MAP_SYSTEM_PER_LANE && !e->ctas_per_sm) bin_ctas[i] = 1;
   }
   int rc = build_work(e, maps);
   if (rc) return rc;

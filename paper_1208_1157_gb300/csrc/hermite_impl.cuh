@@ -609,6 +609,165 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
   }
 }
 
+// Adaptive steps, system per lane, with work handed out per lane: a lane whose system
+// reached its end time (or stopped) takes the bin's next system at once, so the warp does
+// not wait for the lane with the most steps (adaptive step counts differ from system to
+// system).  One loop, each round either loads a new system (that lane only) or takes one
+// step; per system the arithmetic is that of spl_hermite_adaptive_body.
+template <int N>
+__device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, const StepParams &P) {
+  const bool printed = P.corr_form != 0;  // warp-uniform
+  const unsigned FULL = 0xffffffffu;
+  const int SP = B.S_pad;
+  const double tau = fabs(P.dt), dir = P.dt > 0 ? 1.0 : -1.0;
+  const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
+  double x[N][3], v[N][3], m[N], a0[N][3], j0[N][3], kc[N][N];
+  double t = 0.0, te = 0.0;
+  int s = 0, steps = 0;
+  bool has = false, exhausted = false;
+  for (;;) {
+    if (!has && !exhausted) {
+      s = stream_system(B, atomicAdd(P.work_next, 1));
+      if (s < 0) {
+        exhausted = true;
+      } else if (B.status[s] <= SWARM_SYS_DONE) {
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          m[i] = B.m[(size_t)i * SP + s];
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            x[i][c] = B.x[(size_t)(c * N + i) * SP + s];
+            v[i][c] = B.v[(size_t)(c * N + i) * SP + s];
+          }
+        }
+        t = B.t[s];
+        te = adaptive_end(B, P, s);
+        if (!((te - t) * dir > 1e-12 * fmax(1.0, fabs(te)))) {
+          B.status[s] = SWARM_SYS_DONE;
+        } else {
+#pragma unroll
+          for (int i = 1; i < N; i++)
+#pragma unroll
+            for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
+          double q2[N], d2[N][N];
+          spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+          steps = 0;
+          has = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL, has || !exhausted)) break;
+    if (!has) continue;
+    // one step (Eq. 5 length from the start-of-step a0, j0)
+    int code = 0;
+    bool finish = false, reached = false;
+    double ssum = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      ssum += (j0[i][0] * j0[i][0] + j0[i][1] * j0[i][1] + j0[i][2] * j0[i][2]) /
+              (a0[i][0] * a0[i][0] + a0[i][1] * a0[i][1] + a0[i][2] * a0[i][2]);
+    double h = tau * rsqrt(ssum);
+    if (!(h > 0.0) || nonfinite(h)) {
+      code = SWARM_SYS_NONFINITE;
+      finish = true;
+    } else {
+      const double rem = (te - t) * dir;
+      const bool last = h >= rem;
+      h = (last ? rem : h) * dir;
+      const HCoef C = hcoef(h);
+      double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
+          vk[i][c] = fma(j0[i][c], C.h2_2, fma(a0[i][c], C.h, v[i][c]));
+          Vb[i][c] = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
+        }
+      PCoef PC;
+      if (printed) {
+        PC = pcoef(C.h);
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
+      }
+      double q2[N], d2[N][N];
+      for (int ic = 0; ic < P.n_corr; ic++) {
+        double ak[N][3], jk[N][3];
+        spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
+        if (printed) {
+#pragma unroll
+          for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
+        }
+      }
+      spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          x[i][c] = xk[i][c];
+          v[i][c] = vk[i][c];
+        }
+      steps++;
+      t = last ? te : t + h;
+      bool nf = false, ej = false, ce = false;
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
+#pragma unroll
+      for (int i = 1; i < N; i++) ej |= (P.eject2 > 0.0) && (q2[i] > P.eject2);
+#pragma unroll
+      for (int i = 1; i < N; i++)
+#pragma unroll
+        for (int k2 = i + 1; k2 < N; k2++)
+          if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+      code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+      if (!code && P.log_interval > 0 && (steps % P.log_interval) == 0) {
+        double e[4];
+        spl_energy<N>(x, v, m, e);
+        write_log(P, B.gidx[s], t, e);
+      }
+      reached = last && !code;
+      finish = code != 0 || last || steps >= cap;
+    }
+    if (finish) {
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
+          B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
+        }
+      B.t[s] = t;
+      B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+      if (P.counters && steps > 0) {
+        constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+        atomicAdd(&P.counters[0], (unsigned long long)steps);
+        atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)steps * (P.n_corr + 1)));
+      }
+      has = false;
+    }
+  }
+}
+
 // Body per lane with work handed out per system: each of the warp's G groups takes the
 // bin's next system as soon as its own one reached its end time or stopped (fixed steps:
 // stops and per-system end times; adaptive steps: step counts differ from system to
@@ -843,6 +1002,10 @@ __device__ __noinline__ void spl_hermite_adaptive_unit(const BinView &B, const S
 // MINB = 3 is the high-occupancy variant (registers capped for 3 CTAs of 128 threads per SM).
 template <int MAP, int N, int MINB, bool ADAPT = false>
 __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, int nunits, StepParams P) {
+  if (ADAPT && MAP == SWARM_MAP_SYSTEM_PER_LANE) {  // work unit = system (per-lane refill)
+    spl_hermite_adaptive_stream<N>(B, P);
+    return;
+  }
   if (MAP == SWARM_MAP_BODY_PER_LANE) {  // work unit = system (per-group refill)
     bpl_hermite_stream<N, ADAPT>(B, P);
     return;
