@@ -536,6 +536,9 @@ def ncu_case(name):
     elif name == "hermite_adaptive":  # Eq. 5 steps, tau = 0.01, over 1/10 inner period
         ens = ics.three_body(N_SYS, seed=2)
         mapping, steps, integ, dt = S.MAP_SYSTEM_PER_LANE, 1, S.HERMITE4_ADAPTIVE, 0.01
+    elif name == "rkck_adaptive":  # error-controlled steps, tolerance 1e-12, over 1/10 inner period
+        ens = ics.three_body(N_SYS, seed=2)
+        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 1, S.RKCK_ADAPTIVE, 0.05
     elif name == "wide":
         ens = ics.ragged_wide(16384, seed=6)
         mapping, steps, integ, dt = S.MAP_AUTO, 10, S.HERMITE4, DT
@@ -544,7 +547,7 @@ def ncu_case(name):
     with S.Ensemble(ens, stream=stream) as e:
         e.set_option(S.OPT_MAPPING, mapping)
         e.set_stop(3.0, 100.0)
-        t_end = 0.1 * TWO_PI if integ == S.HERMITE4_ADAPTIVE else steps * dt
+        t_end = 0.1 * TWO_PI if integ in (S.HERMITE4_ADAPTIVE, S.RKCK_ADAPTIVE) else steps * dt
         e.integrate(t_end, integ, dt)
         st = e.stats()
     log(f"ncu case {name}: {st}")
@@ -560,7 +563,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged", "rkck", "wide", "hermite_adaptive"])
+    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged", "rkck", "wide", "hermite_adaptive", "rkck_adaptive"])
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
