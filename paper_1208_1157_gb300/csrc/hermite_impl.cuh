@@ -466,6 +466,22 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
   }
 }
 
+// Eq. 5 sum over the bodies of a system held by one lane, sum_i |j_i|^2 / |a_i|^2, with
+// one division: the running fraction num/den takes body i as (num A_i + J_i den)/(den A_i)
+// (A = |a|^2, J = |j|^2; den stays within range for the n <= 4 of this mapping).
+template <int N>
+__device__ __forceinline__ double spl_eq5_sum(const double (&a)[N][3], const double (&j)[N][3]) {
+  double num = 0.0, den = 1.0;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    const double A = fma(a[i][2], a[i][2], fma(a[i][1], a[i][1], a[i][0] * a[i][0]));
+    const double J = fma(j[i][2], j[i][2], fma(j[i][1], j[i][1], j[i][0] * j[i][0]));
+    num = fma(num, A, J * den);
+    den *= A;
+  }
+  return num / den;
+}
+
 template <int N>
 __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, const StepParams &P, int unit) {
   const bool printed = P.corr_form != 0;  // warp-uniform
@@ -504,12 +520,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
   int steps_done = 0, code = 0;
   bool reached = false;
   for (int k = 1; k <= cap; k++) {
-    double ssum = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; i++)
-      ssum += (j0[i][0] * j0[i][0] + j0[i][1] * j0[i][1] + j0[i][2] * j0[i][2]) /
-              (a0[i][0] * a0[i][0] + a0[i][1] * a0[i][1] + a0[i][2] * a0[i][2]);
-    double h = tau * rsqrt(ssum);
+    double h = tau * rsqrt(spl_eq5_sum<N>(a0, j0));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       break;
@@ -661,12 +672,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
     // one step (Eq. 5 length from the start-of-step a0, j0)
     int code = 0;
     bool finish = false, reached = false;
-    double ssum = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; i++)
-      ssum += (j0[i][0] * j0[i][0] + j0[i][1] * j0[i][1] + j0[i][2] * j0[i][2]) /
-              (a0[i][0] * a0[i][0] + a0[i][1] * a0[i][1] + a0[i][2] * a0[i][2]);
-    double h = tau * rsqrt(ssum);
+    double h = tau * rsqrt(spl_eq5_sum<N>(a0, j0));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       finish = true;

@@ -41,14 +41,23 @@ __device__ __forceinline__ double grp_max(double val, int b, int base) {
   return shfl(val, base);
 }
 
-// err^(-1/5) to FP64 accuracy: a single-precision estimate refined by one Newton step on
-// y^-5 = err (y <- y (6 - err y^5) / 5); err in [1e-30, 1e30].
-__device__ __forceinline__ double inv_fifth_root(double err) {
-  const float yf = exp2f(-0.2f * log2f((float)err));
-  double y = (double)yf;
+// e^(-1/10) to FP64 accuracy (the step-control factor err^(-1/5) from the squared error
+// e = err^2): a single-precision estimate refined by one Newton step on y^-10 = e
+// (y <- y (11 - e y^10) / 10); e in [1e-30, 1e30].
+__device__ __forceinline__ double inv_tenth_root(double e) {
+  const float yf = exp2f(-0.1f * log2f((float)e));
+  const double y = (double)yf;
   const double y2 = y * y;
-  const double y5 = y2 * y2 * y;
-  return y * fma(-err, y5, 6.0) * 0.2;
+  const double y4 = y2 * y2;
+  const double y10 = y4 * y4 * y2;
+  return y * fma(-e, y10, 11.0) * 0.1;
+}
+
+// Squared scaled error of a trial, (err / eps)^2 with err = max_b max(|ex_b| / X, |ev_b| / V):
+// from the squared norms, one division and no square root.
+__device__ __forceinline__ double rk_err2(double px, double pv, double X2, double V2, double inv_eps2) {
+  const double inv = 1.0 / (X2 * V2);
+  return fmax(px * (V2 * inv), pv * (X2 * inv)) * inv_eps2;
 }
 
 // One Cash-Karp step of length h from (x, v) with first-stage acceleration a1: writes
@@ -134,6 +143,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
   const unsigned gm = ((1u << N) - 1u) << base;
   const double dir = P.dt > 0 ? 1.0 : -1.0;
   const int nmax = ADAPT ? (P.max_steps > 0 ? P.max_steps : kRkckTrialCap) : 0;
+  const double inv_eps2 = 1.0 / (P.rk_eps * P.rk_eps);
 
   int s = 0;
   bool has = false, exhausted = false;
@@ -219,15 +229,14 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
     double x5[3], v5[3], ex[3], ev[3];
     rkck_stages<N, ADAPT>(x, v, a1, m, b, base, hs, x5, v5, ex, ev);
     bool accept = alive;
-    double err = 0.0;
+    double err = 0.0;  // adaptive: the squared scaled error of the trial
     bool bad = false;
     if (ADAPT) {
       const double X2 = grp_max<N>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2], b, base);
       const double V2 = grp_max<N>(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], b, base);
       const double px = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
       const double pv = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
-      const double rq = grp_max<N>(fmax(px / X2, pv / V2), b, base);
-      err = sqrt(rq) / P.rk_eps;
+      err = grp_max<N>(rk_err2(px, pv, X2, V2, inv_eps2), b, base);  // squared
       bad = nonfinite(err);
       accept = alive && !bad && err <= 1.0;
       if (alive) trials++;
@@ -277,10 +286,10 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
       }
     }
     if (ADAPT && alive && !code && !reached) {
-      double f;
+      double f;  // 0.9 err^(-1/5), from the squared error
       if (err <= 1e-30) f = 5.0;
       else if (err >= 1e30) f = 0.2;
-      else f = 0.9 * inv_fifth_root(err);
+      else f = 0.9 * inv_tenth_root(err);
       h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
       if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) code = SWARM_SYS_NONFINITE;  // step-size underflow
     }

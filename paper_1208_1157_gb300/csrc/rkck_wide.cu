@@ -111,6 +111,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
   double a1[3];
   wring_acc(x, m, b, R, a1, d2s, lane);
   double t = t0, h = fabs(P.dt);
+  const double inv_eps2 = 1.0 / (P.rk_eps * P.rk_eps);
   int steps = 0, trials = 0, code = 0;
   bool reached = false;
   for (int k = 1; k <= nmax; k++) {
@@ -133,8 +134,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
       const double V2 = warp_max(real ? v[0] * v[0] + v[1] * v[1] + v[2] * v[2] : 0.0);
       const double px = ex[0] * ex[0] + ex[1] * ex[1] + ex[2] * ex[2];
       const double pv = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
-      const double rq = warp_max(real ? fmax(px / X2, pv / V2) : 0.0);
-      err = sqrt(rq) / P.rk_eps;
+      err = warp_max(real ? rk_err2(px, pv, X2, V2, inv_eps2) : 0.0);  // squared
       bad = nonfinite(err);
       accept = !bad && err <= 1.0;
       trials++;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
       double f;
       if (err <= 1e-30) f = 5.0;
       else if (err >= 1e30) f = 0.2;
-      else f = 0.9 * inv_fifth_root(err);
+      else f = 0.9 * inv_tenth_root(err);
       h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
       if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) {  // step-size underflow
         code = SWARM_SYS_NONFINITE;
