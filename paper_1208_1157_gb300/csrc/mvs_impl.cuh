@@ -202,8 +202,7 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   double rn[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], g * v[c]);
-  const double rr = sqrt(rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2]);
-  const double rinv = 1.0 / rr;
+  const double rinv = rsqrt(rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2]);
   const double fd = K.smu * x * fma(z, c3, -1.0) * (rinv0 * rinv);
   const double gd = fma(-x2c2, rinv, 1.0);
 #pragma unroll
