@@ -172,8 +172,12 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
 }
 
 // ---------------------------------------------------------------- system per lane
+// The corrector bases Xb, Vb of a step live in registers, or (sb != nullptr) in this
+// lane's column of shared memory (sb[k * 128], k < 6N), which frees 12N registers for a
+// build with more resident warps.
 template <int N>
-__device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepParams &P, int unit) {
+__device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepParams &P, int unit,
+                                                 double *sb = nullptr) {
   const bool printed = P.corr_form != 0;  // warp-uniform
   const int s = unit * 32 + (threadIdx.x & 31);
   if (s >= B.S) return;
@@ -211,14 +215,16 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
   const bool ej_on = P.eject2 > 0.0;
   for (int k = 1; k <= Ns; k++) {
     const HCoef C = (k == Ns && !plan.exact) ? clast : cdt;
-    double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
+    double xk[N][3], vk[N][3], Xr[N][3], Vr[N][3];
+    auto XB = [&](int i, int c) -> double & { return sb ? sb[(i * 3 + c) * 128] : Xr[i][c]; };
+    auto VB = [&](int i, int c) -> double & { return sb ? sb[(3 * N + i * 3 + c) * 128] : Vr[i][c]; };
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
         vk[i][c] = fma(j0[i][c], C.h2_2, fma(a0[i][c], C.h, v[i][c]));
-        Vb[i][c] = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
+        VB(i, c) = fma(j0[i][c], C.h2_12, fma(a0[i][c], C.hh, v[i][c]));
       }
     PCoef PC;
     if (printed) {
@@ -226,12 +232,12 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
+        for (int c = 0; c < 3; c++) XB(i, c) = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
     } else {
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
+        for (int c = 0; c < 3; c++) XB(i, c) = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
@@ -239,17 +245,17 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
+        for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], VB(i, c)));
       if (printed) {
 #pragma unroll
         for (int i = 0; i < N; i++)
 #pragma unroll
-          for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], XB(i, c)));
       } else {
 #pragma unroll
         for (int i = 0; i < N; i++)
 #pragma unroll
-          for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
+          for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], XB(i, c)));
       }
     }
     spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
@@ -1012,6 +1018,9 @@ __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, i
     spl_hermite_adaptive_stream<N>(B, P);
     return;
   }
+  // the high-occupancy system-per-lane build keeps the corrector bases in shared memory
+  constexpr bool kSmemBases = !ADAPT && MAP == SWARM_MAP_SYSTEM_PER_LANE && MINB >= 3;
+  __shared__ double sbases[kSmemBases ? 6 * N * 128 : 1];
   if (MAP == SWARM_MAP_BODY_PER_LANE) {  // work unit = system (per-group refill)
     bpl_hermite_stream<N, ADAPT>(B, P);
     return;
@@ -1026,7 +1035,7 @@ __global__ void __launch_bounds__(128, MINB) hermite_uniform_kernel(BinView B, i
       if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_adaptive_body<N>(B, P, w);
       else bpl_hermite_adaptive_body<N>(B, P, w);
     } else {
-      if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_body<N>(B, P, w);
+      if (MAP == SWARM_MAP_SYSTEM_PER_LANE) spl_hermite_body<N>(B, P, w, kSmemBases ? sbases + threadIdx.x : nullptr);
       else bpl_hermite_body<N>(B, P, w);
     }
   }
