@@ -169,19 +169,26 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   if (on && !have_chi) x = chi_guess(K, r, v, r0, sig0, alpha, h);
   bool done = !on;
   int it = 0;
+  // universal functions U0..U3 (U_k = chi^k c_k(alpha chi^2)) at the last iterate and its
+  // Newton correction: with U3' = U2, U2' = U1, U1' = U0, U0' = -alpha U1 they move to the
+  // root by a second-order Taylor step, which is exact to rounding for the small final
+  // corrections (|d chi| <= 1e-6 max(1, |chi|), dropped terms ~ d chi^3)
+  double U0 = 1.0, U1 = 0.0, U2 = 0.0, U3 = 0.0, dx = 0.0;
   for (int i = 0; i < 50; i++) {
     if (__all_sync(0xffffffffu, done)) break;
     if (!done) {
-      double x2 = x * x;
-      double z = alpha * x2;
+      const double x2 = x * x;
+      const double z = alpha * x2;
       double c2, c3;
       stumpff23(z, c2, c3);
-      double x3 = x2 * x;
-      double F = fma(s0 * x2, c2, fma(beta * x3, c3, fma(r0, x, -target)));
-      const double u1 = fma(-z, c3, 1.0);  // U1 / chi
-      double dF = fma(s0 * x, u1, fma(beta * x2, c2, r0));
-      const double ddF = fma(s0, fma(-z, c2, 1.0), beta * x * u1);
-      double dx = F / dF;
+      U0 = fma(-z, c2, 1.0);
+      U1 = x * fma(-z, c3, 1.0);
+      U2 = x2 * c2;
+      U3 = x2 * x * c3;
+      const double F = fma(s0, U2, fma(beta, U3, fma(r0, x, -target)));
+      const double dF = fma(s0, U1, fma(beta, U2, r0));  // |r(chi)|
+      const double ddF = fma(s0, U0, beta * U1);
+      dx = F / dF;
       x -= dx;
       it++;
       const double tol = fmax(1.0, fabs(x));
@@ -191,20 +198,30 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   iters = it;
   if (!on) return true;
   if (!done) return false;
-  const double x2 = x * x;
-  const double z = alpha * x2;
-  double c2, c3;
-  stumpff23(z, c2, c3);
-  const double x2c2 = x2 * c2;
-  const double x3c3 = x2 * x * c3;
-  const double f = fma(-x2c2, rinv0, 1.0);
-  const double g = fma(-x3c3, K.smuinv, h);
+  if (fabs(dx) <= 1e-6 * fmax(1.0, fabs(x))) {
+    const double d2h = 0.5 * dx * dx;
+    const double U1n = fma(-alpha * U1, d2h, fma(-U0, dx, U1));
+    const double U2n = fma(U0, d2h, fma(-U1, dx, U2));
+    U3 = fma(U1, d2h, fma(-U2, dx, U3));
+    U1 = U1n;
+    U2 = U2n;
+  } else {  // a large last correction: evaluate at the root
+    const double x2 = x * x;
+    const double z = alpha * x2;
+    double c2, c3;
+    stumpff23(z, c2, c3);
+    U1 = x * fma(-z, c3, 1.0);
+    U2 = x2 * c2;
+    U3 = x2 * x * c3;
+  }
+  const double f = fma(-U2, rinv0, 1.0);
+  const double g = fma(-U3, K.smuinv, h);
   double rn[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], g * v[c]);
   const double rinv = rsqrt(rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2]);
-  const double fd = K.smu * x * fma(z, c3, -1.0) * (rinv0 * rinv);
-  const double gd = fma(-x2c2, rinv, 1.0);
+  const double fd = -K.smu * U1 * (rinv0 * rinv);
+  const double gd = fma(-U2, rinv, 1.0);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     v[c] = fma(fd, r[c], gd * v[c]);
