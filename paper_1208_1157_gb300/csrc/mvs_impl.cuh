@@ -150,12 +150,19 @@ static __device__ __noinline__ double chi_guess(const KepConst &K, const double 
 // the step, which for Newton is (F''/2F') d chi^2 with F'' = s0 (1 - z c2) + beta chi
 // (1 - z c3), is below 1e-15 max(1, |chi|): the same root to the same tolerance, usually
 // one iteration sooner (the oracle only uses the first test); then the Lagrange f, g,
-// fdot, gdot.  `chi` carries the previous step's solution as the starting point (warm
-// start; `have_chi` false on the first step of a call).  Executed by every lane of the
+// fdot, gdot.  `cs` carries the previous solutions as the starting point (none on the
+// first step of a call: Vallado's guess).  Executed by every lane of the
 // warp; lanes with `on` false do not change their state.  Returns false on
 // non-convergence in 50 iterations.
-static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, double (&r)[3], double (&v)[3], double h, double &chi,
-                             bool have_chi, int &iters) {
+// Starting point of the next Kepler solve of a planet: its last two solutions, which
+// (steps of equal length) extrapolate linearly to within the orbit's second difference.
+struct ChiState {
+  double chi = 0.0, prev = 0.0;
+  int n = 0;  // solutions held (0, 1, 2)
+};
+
+static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, double (&r)[3], double (&v)[3], double h,
+                                                 ChiState &cs, int &iters) {
   const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
   const double rinv0 = rsqrt(r2);
   const double r0 = r2 * rinv0;
@@ -165,8 +172,8 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   const double s0 = sig0 * K.smuinv;
   const double beta = fma(-alpha, r0, 1.0);
   const double target = K.smu * h;
-  double x = chi;
-  if (on && !have_chi) x = chi_guess(K, r, v, r0, sig0, alpha, h);
+  double x = cs.n >= 2 ? 2.0 * cs.chi - cs.prev : cs.chi;
+  if (on && cs.n == 0) x = chi_guess(K, r, v, r0, sig0, alpha, h);
   bool done = !on;
   int it = 0;
   // universal functions U0..U3 (U_k = chi^k c_k(alpha chi^2)) at the last iterate and its
@@ -227,7 +234,9 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
     v[c] = fma(fd, r[c], gd * v[c]);
     r[c] = rn[c];
   }
-  chi = x;
+  cs.prev = cs.chi;
+  cs.chi = x;
+  cs.n = cs.n < 2 ? cs.n + 1 : 2;
   return true;
 }
 
@@ -408,8 +417,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
 
   bool alive = runnable;
   int steps_done = 0;
-  double chi = 0.0;
-  bool have_chi = false;
+  ChiState cs;
   unsigned long long kep_iters = 0;
 
   for (int k = 1; k <= Nmax; k++) {
@@ -435,8 +443,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     // Keplerian drift of every planet
     int its = 0;
-    bool ok = kepler_drift(active && b != 0, K, q, u, h, chi, have_chi, its);
-    have_chi = true;
+    bool ok = kepler_drift(active && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
     // accelerations at the new positions, reused by the next step's first kick
     mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
@@ -589,8 +596,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
   double t0 = 0.0;
   int kg = 0;
   double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
-  double chi = 0.0;
-  bool have_chi = false;
+  ChiState cs;
   unsigned long long kep_iters = 0;
 #pragma unroll
   for (int r = 0; r < RTA; r++) kc[r] = 0.0;
@@ -656,8 +662,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
           u[c] = un[c];
           acc[c] = an[c];
         }
-        chi = 0.0;
-        have_chi = false;
+        cs = ChiState();
         has = plan.N > 0;
         if (runnable && plan.N == 0 && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
       }
@@ -684,8 +689,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(active && b != 0, K, q, u, h, chi, have_chi, its);
-    if (active) have_chi = true;
+    const bool ok = kepler_drift(active && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
     double Q[3], d2[RTA];
 #pragma unroll

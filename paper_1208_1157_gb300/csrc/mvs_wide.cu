@@ -202,8 +202,7 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
   double q[3], u[3], acc[3], Q[3];
   wide_to_canonical<JAC>(x, v, W, b, real, lane, q, u);
   wide_mvs_acc<JAC>(q, W, b, n, real, lane, acc, Q, d2s);
-  double chi = 0.0;
-  bool have_chi = false;
+  ChiState cs;
   unsigned long long kep_iters = 0;
   int steps = 0, code = 0;
   for (int k = 1; k <= plan.N; k++) {
@@ -223,8 +222,7 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(real && b != 0, K, q, u, h, chi, have_chi, its);
-    have_chi = true;
+    const bool ok = kepler_drift(real && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
     wide_mvs_acc<JAC>(q, W, b, n, real, lane, acc, Q, d2s);
 #pragma unroll
