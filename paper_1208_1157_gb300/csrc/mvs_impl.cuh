@@ -146,14 +146,6 @@ static __device__ __noinline__ double chi_guess(const KepConst &K, const double 
 
 // Universal-variable Kepler drift of (r, v) by h: Newton on
 //   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
-// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|), or until the error left after
-// the step, which for Newton is (F''/2F') d chi^2 with F'' = s0 (1 - z c2) + beta chi
-// (1 - z c3), is below 1e-15 max(1, |chi|): the same root to the same tolerance, usually
-// one iteration sooner (the oracle only uses the first test); then the Lagrange f, g,
-// fdot, gdot.  `cs` carries the previous solutions as the starting point (none on the
-// first step of a call: Vallado's guess).  Executed by every lane of the
-// warp; lanes with `on` false do not change their state.  Returns false on
-// non-convergence in 50 iterations.
 // Starting point of the next Kepler solve of a planet: its last two solutions, which
 // (steps of equal length) extrapolate linearly to within the orbit's second difference.
 struct ChiState {
@@ -161,6 +153,16 @@ struct ChiState {
   int n = 0;  // solutions held (0, 1, 2)
 };
 
+// Universal-variable Kepler drift of (r, v) by h: Newton on
+//   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
+// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|), or until the error left after
+// the step, which for Newton is (F''/2F') d chi^2 with F'' = s0 (1 - z c2) + beta chi
+// (1 - z c3), is below 1e-16 |chi| (half an ulp of chi: the root to rounding, the one the
+// oracle's first test alone reaches, usually one iteration sooner); then the Lagrange f,
+// g, fdot, gdot.  `cs` carries the previous solutions as the starting point (none on the
+// first step of a call: Vallado's guess).  Executed by every lane of the warp; lanes with
+// `on` false do not change their state.  Returns false on non-convergence in 50
+// iterations.
 static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, double (&r)[3], double (&v)[3], double h,
                                                  ChiState &cs, int &iters) {
   const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
@@ -198,8 +200,7 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
       dx = F / dF;
       x -= dx;
       it++;
-      const double tol = fmax(1.0, fabs(x));
-      if (fabs(dx) <= 1e-14 * tol || fabs(ddF) * (dx * dx) <= 2e-15 * tol * fabs(dF)) done = true;
+      if (fabs(dx) <= 1e-14 * fmax(1.0, fabs(x)) || fabs(ddF) * (dx * dx) <= 2e-16 * fabs(x) * fabs(dF)) done = true;
     }
   }
   iters = it;
