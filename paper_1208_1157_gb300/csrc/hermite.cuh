@@ -54,25 +54,26 @@ __device__ __forceinline__ HCoef hsel(bool p, const HCoef &a, const HCoef &b) {
 //   dx = x_j - x_i, dv = v_j - v_i, rho = 1/|dx|,
 //   w  = dv - 3 (dx.dv)/|dx|^2 dx   so that   a_i += m_j rho^3 dx,  jerk_i += m_j rho^3 w
 // and the partner receives the opposite terms scaled by m_i.
-__device__ __forceinline__ void pair_geom(const double (&xi)[3], const double (&vi)[3], const double (&xj)[3],
-                                          const double (&vj)[3], double (&dx)[3], double (&w)[3], double &rho3,
-                                          double &r2) {
+// Products and differences in the DFMA forms of `kmul` / `ksub` (same values).
+__device__ __forceinline__ void pair_geom(const F64k &k, const double (&xi)[3], const double (&vi)[3],
+                                          const double (&xj)[3], const double (&vj)[3], double (&dx)[3],
+                                          double (&w)[3], double &rho3, double &r2) {
   double dv[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    dx[c] = xj[c] - xi[c];
-    dv[c] = vj[c] - vi[c];
+    dx[c] = ksub(k, xj[c], xi[c]);
+    dv[c] = ksub(k, vj[c], vi[c]);
   }
-  r2 = dx[0] * dx[0];
+  r2 = kmul(k, dx[0], dx[0]);
   r2 = fma(dx[1], dx[1], r2);
   r2 = fma(dx[2], dx[2], r2);
-  double rv = dx[0] * dv[0];
+  double rv = kmul(k, dx[0], dv[0]);
   rv = fma(dx[1], dv[1], rv);
   rv = fma(dx[2], dv[2], rv);
   double rho = rsqrt(r2);
-  double rho2 = rho * rho;
-  rho3 = rho2 * rho;
-  double cc = -3.0 * (rv * rho2);
+  double rho2 = kmul(k, rho, rho);
+  rho3 = kmul(k, rho2, rho);
+  double cc = kmul(k, -3.0, kmul(k, rv, rho2));
 #pragma unroll
   for (int c = 0; c < 3; c++) w[c] = fma(cc, dx[c], dv[c]);
 }
@@ -133,7 +134,7 @@ struct Ring {
 // MON: also return q2 (squared distance of this body to body 0) and d2[r] (squared
 // distance of this lane's pair in round r) for the monitor.
 template <int N, bool MON>
-__device__ __forceinline__ void ring_accjerk(const double (&x)[3], const double (&v)[3], double m, int b, int base,
+__device__ __forceinline__ void ring_accjerk(const F64k &k, const double (&x)[3], const double (&v)[3], double m, int b, int base,
                                              double (&a)[3], double (&jk)[3], double &q2,
                                              double (&d2)[Ring<N>::RT > 0 ? Ring<N>::RT : 1]) {
 #pragma unroll
@@ -156,9 +157,9 @@ __device__ __forceinline__ void ring_accjerk(const double (&x)[3], const double 
     }
     double mj = shfl(m, base + p);
     double dx[3], w[3], rho3, r2;
-    pair_geom(x, v, xj, vj, dx, w, rho3, r2);
-    double sj = mj * rho3;
-    double si = m * rho3;
+    pair_geom(k, x, v, xj, vj, dx, w, rho3, r2);
+    double sj = kmul(k, mj, rho3);
+    double si = kmul(k, m, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       a[c] = fma(sj, dx[c], a[c]);
@@ -196,8 +197,8 @@ __device__ __forceinline__ void ring_accjerk(const double (&x)[3], const double 
     }
     double mj = shfl(m, base + p);
     double dx[3], w[3], rho3, r2;
-    pair_geom(x, v, xj, vj, dx, w, rho3, r2);
-    double sj = mj * rho3;
+    pair_geom(k, x, v, xj, vj, dx, w, rho3, r2);
+    double sj = kmul(k, mj, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       a[c] = fma(sj, dx[c], a[c]);
@@ -247,7 +248,7 @@ __device__ __forceinline__ void ring_energy(const double (&x)[3], const double (
 // One lane integrates a whole system held in registers; pairs in the order
 // planet-planet first, then star-planet, so every body's star term comes last (Sec. 4.2).
 template <int N>
-__device__ __forceinline__ void spl_accjerk(const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
+__device__ __forceinline__ void spl_accjerk(const F64k &kk, const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
                                             double (&a)[N][3], double (&jk)[N][3], double (&q2)[N],
                                             double (&d2)[N][N]) {
 #pragma unroll
@@ -262,8 +263,8 @@ __device__ __forceinline__ void spl_accjerk(const double (&x)[N][3], const doubl
 #pragma unroll
     for (int k = i + 1; k < N; k++) {
       double dx[3], w[3], rho3, r2;
-      pair_geom(x[i], v[i], x[k], v[k], dx, w, rho3, r2);
-      double sk = m[k] * rho3, si = m[i] * rho3;
+      pair_geom(kk, x[i], v[i], x[k], v[k], dx, w, rho3, r2);
+      double sk = kmul(kk, m[k], rho3), si = kmul(kk, m[i], rho3);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         a[i][c] = fma(sk, dx[c], a[i][c]);
@@ -276,8 +277,8 @@ __device__ __forceinline__ void spl_accjerk(const double (&x)[N][3], const doubl
 #pragma unroll
   for (int k = 1; k < N; k++) {
     double dx[3], w[3], rho3, r2;
-    pair_geom(x[0], v[0], x[k], v[k], dx, w, rho3, r2);
-    double sk = m[k] * rho3, s0 = m[0] * rho3;
+    pair_geom(kk, x[0], v[0], x[k], v[k], dx, w, rho3, r2);
+    double sk = kmul(kk, m[k], rho3), s0 = kmul(kk, m[0], rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       a[0][c] = fma(sk, dx[c], a[0][c]);

@@ -59,7 +59,7 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
   }
 
   double a0[3], j0[3], q2, d2[RT];
-  ring_accjerk<N, false>(x, v, m, b, base, a0, j0, q2, d2);
+  ring_accjerk<N, false>(P.fk, x, v, m, b, base, a0, j0, q2, d2);
   const HCoef cdt = hcoef(P.dt);
   const HCoef clast = hcoef(plan.h_last);
   bool alive = runnable;
@@ -89,7 +89,7 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
     // corrector passes (time-symmetric form of Eq. 4)
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[3], jk[3];
-      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+      ring_accjerk<N, false>(P.fk, xk, vk, m, b, base, ak, jk, q2, d2);
 #pragma unroll
       for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
       if (printed) {
@@ -102,7 +102,7 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
     }
     // third evaluation: next step's a0, j0 and the monitor's distances
     double an[3], jn[3];
-    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    ring_accjerk<N, true>(P.fk, xk, vk, m, b, base, an, jn, q2, d2);
     if (active) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -207,7 +207,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
 
   double a0[N][3], j0[N][3], q2[N], d2[N][N];
-  spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+  spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
   const HCoef cdt = hcoef(P.dt);
   const HCoef clast = hcoef(plan.h_last);
   int steps_done = 0;
@@ -241,7 +241,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
-      spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+      spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
@@ -258,7 +258,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
           for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], XB(i, c)));
       }
     }
-    spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+    spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
@@ -364,7 +364,7 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
     kc[r - 1] = (b != 0 && p != 0 && RT == R::RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
   }
   double a0[3], j0[3], q2, d2[RT];
-  ring_accjerk<N, false>(x, v, m, b, base, a0, j0, q2, d2);
+  ring_accjerk<N, false>(P.fk, x, v, m, b, base, a0, j0, q2, d2);
   const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
   double t = t0;
   int steps_done = 0, code = 0;
@@ -398,7 +398,7 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[3], jk[3];
-      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+      ring_accjerk<N, false>(P.fk, xk, vk, m, b, base, ak, jk, q2, d2);
 #pragma unroll
       for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
       if (printed) {
@@ -410,7 +410,7 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
       }
     }
     double an[3], jn[3];
-    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    ring_accjerk<N, true>(P.fk, xk, vk, m, b, base, an, jn, q2, d2);
     const bool active = alive && !bad;
     if (active) {
 #pragma unroll
@@ -520,7 +520,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
 #pragma unroll
     for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
   double a0[N][3], j0[N][3], q2[N], d2[N][N];
-  spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+  spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
   const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
   double t = t0;
   int steps_done = 0, code = 0;
@@ -559,7 +559,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
-      spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+      spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
@@ -576,7 +576,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
           for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
       }
     }
-    spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+    spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
@@ -667,7 +667,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
 #pragma unroll
             for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
           double q2[N], d2[N][N];
-          spl_accjerk<N>(x, v, m, a0, j0, q2, d2);
+          spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
           steps = 0;
           has = true;
         }
@@ -712,7 +712,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
       double q2[N], d2[N][N];
       for (int ic = 0; ic < P.n_corr; ic++) {
         double ak[N][3], jk[N][3];
-        spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+        spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
         for (int i = 0; i < N; i++)
 #pragma unroll
@@ -729,7 +729,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
             for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
         }
       }
-      spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+      spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
       for (int i = 0; i < N; i++)
 #pragma unroll
@@ -852,7 +852,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
         if (take) kc[r - 1] = k;
       }
       double an[3], jn[3], q2, d2[RT];
-      ring_accjerk<N, false>(x, v, m, b, base, an, jn, q2, d2);
+      ring_accjerk<N, false>(P.fk, x, v, m, b, base, an, jn, q2, d2);
       if (take) {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -916,7 +916,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
     double q2, d2[RT];
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[3], jk[3];
-      ring_accjerk<N, false>(xk, vk, m, b, base, ak, jk, q2, d2);
+      ring_accjerk<N, false>(P.fk, xk, vk, m, b, base, ak, jk, q2, d2);
 #pragma unroll
       for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
       if (printed) {
@@ -928,7 +928,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
       }
     }
     double an[3], jn[3];
-    ring_accjerk<N, true>(xk, vk, m, b, base, an, jn, q2, d2);
+    ring_accjerk<N, true>(P.fk, xk, vk, m, b, base, an, jn, q2, d2);
     const bool active = alive && !bad;
     if (active) {
 #pragma unroll

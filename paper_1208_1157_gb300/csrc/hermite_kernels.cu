@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128) plain_prepare_kernel(BinView B, StepParam
   W.t0[s] = B.t[s];
   atomicMax(W.max_steps, Ns);
   double a[N][3], j[N][3], q2[N], d2[N][N];
-  spl_accjerk<N>(x, v, m, a, j, q2, d2);
+  spl_accjerk<N>(P.fk, x, v, m, a, j, q2, d2);
 #pragma unroll
   for (int i = 0; i < N; i++)
 #pragma unroll
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(128) plain_step_kernel(BinView B, StepParams P
   double q2[N], d2[N][N];
   for (int ic = 0; ic < P.n_corr; ic++) {
     double ak[N][3], jk[N][3];
-    spl_accjerk<N>(xk, vk, m, ak, jk, q2, d2);
+    spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) plain_step_kernel(BinView B, StepParams P
         xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
       }
   }
-  spl_accjerk<N>(xk, vk, m, a0, j0, q2, d2);
+  spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
   bool nf = false, ej = false, ce = false;
 #pragma unroll
   for (int i = 0; i < N; i++)

@@ -38,7 +38,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // distance to body 0) and, per round r, the squared distance of this lane's pair
 // (b, b + r mod n) in d2s[(r - 1) * 32 + lane].
 template <bool MON>
-__device__ __forceinline__ void wring_accjerk(const double (&x)[3], const double (&v)[3], double m, int b,
+__device__ __forceinline__ void wring_accjerk(const F64k &k, const double (&x)[3], const double (&v)[3], double m, int b,
                                               const WideRing &R, double (&a)[3], double (&jk)[3], double &q2,
                                               double *d2s, int lane) {
 #pragma unroll
@@ -63,15 +63,15 @@ __device__ __forceinline__ void wring_accjerk(const double (&x)[3], const double
     }
     const double mj = shfl(m, p);
     double dx[3], w[3], rho3, r2;
-    pair_geom(x, v, xj, vj, dx, w, rho3, r2);
-    const double sj = mj * rho3;
+    pair_geom(k, x, v, xj, vj, dx, w, rho3, r2);
+    const double sj = kmul(k, mj, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       a[c] = fma(sj, dx[c], a[c]);
       jk[c] = fma(sj, w[c], jk[c]);
     }
     if (full) {  // reaction from lane q, which evaluated the pair (q, b)
-      const double si = m * rho3;
+      const double si = kmul(k, m, rho3);
       double rdx[3], rw[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -230,7 +230,7 @@ __device__ __forceinline__ void wide_hermite_body(const BinView &B, const StepPa
   __syncwarp();
 
   double a0[3], j0[3], q2;
-  wring_accjerk<false>(x, v, m, b, R, a0, j0, q2, d2s, lane);
+  wring_accjerk<false>(P.fk, x, v, m, b, R, a0, j0, q2, d2s, lane);
   const HCoef cdt = hcoef(P.dt);
   const HCoef clast = hcoef(ADAPT ? P.dt : plan.h_last);
   double t = t0;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void wide_hermite_body(const BinView &B, const StepPa
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[3], jk[3];
-      wring_accjerk<false>(xk, vk, m, b, R, ak, jk, q2, d2s, lane);
+      wring_accjerk<false>(P.fk, xk, vk, m, b, R, ak, jk, q2, d2s, lane);
 #pragma unroll
       for (int c = 0; c < 3; c++) vk[c] = fma(-C.h2_12, jk[c], fma(C.hh, ak[c], Vb[c]));
       if (printed) {
@@ -287,7 +287,7 @@ __device__ __forceinline__ void wide_hermite_body(const BinView &B, const StepPa
     }
     // third evaluation: next step's a0, j0 and the monitor's distances
     double an[3], jn[3];
-    wring_accjerk<true>(xk, vk, m, b, R, an, jn, q2, d2s, lane);
+    wring_accjerk<true>(P.fk, xk, vk, m, b, R, an, jn, q2, d2s, lane);
     __syncwarp();
     if (!bad) {
 #pragma unroll
