@@ -38,16 +38,17 @@ __device__ __forceinline__ int stream_system(const BinView &B, int k) {
   return k < B.S ? k : -1;
 }
 
-// FP64 constants 0 and -1 held in the kernel's parameters, so the compiler cannot fold
-// them: a product written fma(a, b, zero) and a difference written fma(b, mone, a) stay
-// DFMA instructions, which the FP64 pipe issues at 2 per clock per SM against ~1.69 for
-// DMUL and DADD.  fma(b, -1, a) is a - b exactly; fma(a, b, +0) is a * b except that an
-// exact zero product comes out +0.
+// FP64 constants 0, -1 and 1 held in the kernel's parameters, so the compiler cannot
+// fold them: a product written fma(a, b, zero), a difference fma(b, mone, a) and a sum
+// fma(a, one, b) stay DFMA instructions, which the FP64 pipe issues at 2 per clock per SM
+// against ~1.69 for DMUL and DADD.  fma(b, -1, a) is a - b and fma(a, 1, b) is a + b
+// exactly; fma(a, b, +0) is a * b except that an exact zero product comes out +0.
 struct F64k {
-  double zero, mone;
+  double zero, mone, one;
 };
 __device__ __forceinline__ double kmul(const F64k &k, double a, double b) { return fma(a, b, k.zero); }
 __device__ __forceinline__ double ksub(const F64k &k, double a, double b) { return fma(b, k.mone, a); }
+__device__ __forceinline__ double kadd(const F64k &k, double a, double b) { return fma(a, k.one, b); }
 
 struct StepParams {
   double t_end, dt;
@@ -65,7 +66,7 @@ struct StepParams {
   int max_steps = 0;     // cap on the steps one launch takes per system (0: none)
   const double *t_end_dev = nullptr;  // end time read from device memory (graph replays)
   double rk_eps = 1e-12;  // error tolerance of the adaptive Runge-Kutta Cash-Karp step
-  F64k fk = {0.0, -1.0};  // opaque constants (set on the host, never changed)
+  F64k fk = {0.0, -1.0, 1.0};  // opaque constants (set on the host, never changed)
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }

@@ -92,6 +92,17 @@ __device__ __forceinline__ double grp_sum(double val, int b, int base) {
   return shfl(val, base);
 }
 
+// the same sum with the additions as DFMA
+template <int N>
+__device__ __forceinline__ double grp_sum(const F64k &k, double val, int b, int base) {
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, val, off);
+    val = kadd(k, (b + off < N) ? o : 0.0, val);
+  }
+  return shfl(val, base);
+}
+
 // exclusive prefix sum over the group (lane b gets the sum over lanes 0..b-1)
 template <int N>
 __device__ __forceinline__ double grp_scan_excl(double val, int b) {
@@ -100,6 +111,18 @@ __device__ __forceinline__ double grp_scan_excl(double val, int b) {
   for (int off = 1; off < N; off <<= 1) {
     double o = __shfl_up_sync(0xffffffffu, inc, off);
     inc += (b >= off) ? o : 0.0;
+  }
+  double ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  return b > 0 ? ex : 0.0;
+}
+
+template <int N>
+__device__ __forceinline__ double grp_scan_excl(const F64k &k, double val, int b) {
+  double inc = val;
+#pragma unroll
+  for (int off = 1; off < N; off <<= 1) {
+    double o = __shfl_up_sync(0xffffffffu, inc, off);
+    inc = kadd(k, (b >= off) ? o : 0.0, inc);
   }
   double ex = __shfl_up_sync(0xffffffffu, inc, 1);
   return b > 0 ? ex : 0.0;
@@ -315,9 +338,9 @@ __device__ __forceinline__ void spl_energy(const double (&x)[N][3], const double
 // Close-encounter test of one planet pair: |x_i - x_j| < f k_ij (q_i + q_j)/2 with
 // kc = (f k_ij / 2)^2, k_ij = ((m_i + m_j)/(3 m_0))^(1/3).  The bound
 // (q_i + q_j)^2 <= 2 (q_i^2 + q_j^2) rules most pairs out without a square root.
-__device__ __forceinline__ bool close_encounter(double d2, double kc, double q2i, double q2j) {
-  double t = q2i + q2j;
-  if (d2 < 2.0 * kc * t) {
+__device__ __forceinline__ bool close_encounter(const F64k &k, double d2, double kc, double q2i, double q2j) {
+  double t = kadd(k, q2i, q2j);
+  if (d2 < kmul(k, kmul(k, 2.0, kc), t)) {
     double s = sqrt(q2i) + sqrt(q2j);
     return d2 < kc * (s * s);
   }

@@ -123,7 +123,7 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
       int p = b + r;
       if (p >= N) p -= N;
       double q2p = shfl(q2, base + p);
-      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
     }
     const unsigned gm = ((1u << N) - 1u) << base;
     const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
@@ -278,7 +278,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     for (int i = 1; i < N; i++)
 #pragma unroll
       for (int k2 = i + 1; k2 < N; k2++)
-        if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+        if (kc[i][k2] > 0.0 && close_encounter(P.fk, d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
     code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (code) break;
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
@@ -432,7 +432,7 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
       int p = b + r;
       if (p >= N) p -= N;
       double q2p = shfl(q2, base + p);
-      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
     }
     const unsigned gm = ((1u << N) - 1u) << base;
     const unsigned bnf = __ballot_sync(FULL, alive && (nf || bad)) & gm;
@@ -597,7 +597,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     for (int i = 1; i < N; i++)
 #pragma unroll
       for (int k2 = i + 1; k2 < N; k2++)
-        if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+        if (kc[i][k2] > 0.0 && close_encounter(P.fk, d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
     code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (code) break;
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
@@ -750,7 +750,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
       for (int i = 1; i < N; i++)
 #pragma unroll
         for (int k2 = i + 1; k2 < N; k2++)
-          if (kc[i][k2] > 0.0 && close_encounter(d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+          if (kc[i][k2] > 0.0 && close_encounter(P.fk, d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
       code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
       if (!code && P.log_interval > 0 && (steps % P.log_interval) == 0) {
         double e[4];
@@ -950,7 +950,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
       int p = b + r;
       if (p >= N) p -= N;
       double q2p = shfl(q2, base + p);
-      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
     }
     const unsigned bnf = __ballot_sync(FULL, alive && (nf || bad)) & gm;
     const unsigned bej = __ballot_sync(FULL, active && ej) & gm;

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128) plain_step_kernel(BinView B, StepParams P
 #pragma unroll
     for (int k2 = i + 1; k2 < N; k2++) {
       double kc = hill_kc(P.ce_factor, m[i], m[k2], m[0]);
-      if (kc > 0.0 && close_encounter(d2[i][k2], kc, q2[i], q2[k2])) ce = true;
+      if (kc > 0.0 && close_encounter(P.fk, d2[i][k2], kc, q2[i], q2[k2])) ce = true;
     }
   const int code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
   const double te = P.t_end_dev ? *P.t_end_dev : P.t_end;  // device copy when replayed from a graph

@@ -98,8 +98,8 @@ __device__ __forceinline__ void wring_accjerk(const F64k &k, const double (&x)[3
 
 // Acceleration only (Eq. 1) of body b, with the pair distances of each round in
 // d2s[(r - 1) * 32 + lane] (used by the monitor when the state is the accepted one).
-__device__ __forceinline__ void wring_acc(const double (&x)[3], double m, int b, const WideRing &R, double (&a)[3],
-                                          double *d2s, int lane) {
+__device__ __forceinline__ void wring_acc(const F64k &k, const double (&x)[3], double m, int b, const WideRing &R,
+                                          double (&a)[3], double *d2s, int lane) {
 #pragma unroll
   for (int c = 0; c < 3; c++) a[c] = 0.0;
 #pragma unroll
@@ -112,18 +112,18 @@ __device__ __forceinline__ void wring_acc(const double (&x)[3], double m, int b,
     if (q < 0) q += R.n;
     double dx[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], p) - x[c];
+    for (int c = 0; c < 3; c++) dx[c] = ksub(k, shfl(x[c], p), x[c]);
     const double mp = shfl(m, p);
-    double r2 = dx[0] * dx[0];
+    double r2 = kmul(k, dx[0], dx[0]);
     r2 = fma(dx[1], dx[1], r2);
     r2 = fma(dx[2], dx[2], r2);
     const double rho = rsqrt(r2);
-    const double rho3 = rho * rho * rho;
-    const double sp = mp * rho3;
+    const double rho3 = kmul(k, kmul(k, rho, rho), rho);
+    const double sp = kmul(k, mp, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
     if (full) {  // reaction from lane q, which evaluated the pair (q, b)
-      const double si = m * rho3;
+      const double si = kmul(k, m, rho3);
       double rdx[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) rdx[c] = shfl(dx[c], q);
@@ -313,7 +313,7 @@ __device__ __forceinline__ void wide_hermite_body(const BinView &B, const StepPa
       if (p >= n) p -= n;
       const double q2p = shfl(q2, p);
       const double kc = kcs[(r - 1) * 32 + lane];
-      if (kc > 0.0 && close_encounter(d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
+      if (kc > 0.0 && close_encounter(P.fk, d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
     }
     const unsigned bnf = __ballot_sync(FULL, nf || bad) & gm;
     const unsigned bej = __ballot_sync(FULL, ej) & gm;

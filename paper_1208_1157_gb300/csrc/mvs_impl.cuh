@@ -25,7 +25,7 @@ struct ARing {
 };
 
 template <int M, int OFF>
-__device__ __forceinline__ void ring_acc(const double (&x)[3], double m, int j, int base, double (&a)[3],
+__device__ __forceinline__ void ring_acc(const F64k &k, const double (&x)[3], double m, int j, int base, double (&a)[3],
                                          double (&d2)[ARing<M>::RTA]) {
 #pragma unroll
   for (int c = 0; c < 3; c++) a[c] = 0.0;
@@ -37,14 +37,14 @@ __device__ __forceinline__ void ring_acc(const double (&x)[3], double m, int j, 
     if (q < 0) q += M;
     double dx[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], base + OFF + p) - x[c];
+    for (int c = 0; c < 3; c++) dx[c] = ksub(k, shfl(x[c], base + OFF + p), x[c]);
     double mp = shfl(m, base + OFF + p);
-    double r2 = dx[0] * dx[0];
+    double r2 = kmul(k, dx[0], dx[0]);
     r2 = fma(dx[1], dx[1], r2);
     r2 = fma(dx[2], dx[2], r2);
     double rho = rsqrt(r2);
-    double rho3 = rho * rho * rho;
-    double sp = mp * rho3, si = m * rho3;
+    double rho3 = kmul(k, kmul(k, rho, rho), rho);
+    double sp = kmul(k, mp, rho3), si = kmul(k, m, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
     double rdx[3];
@@ -61,13 +61,13 @@ __device__ __forceinline__ void ring_acc(const double (&x)[3], double m, int j, 
     if (p >= M) p -= M;
     double dx[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], base + OFF + p) - x[c];
+    for (int c = 0; c < 3; c++) dx[c] = ksub(k, shfl(x[c], base + OFF + p), x[c]);
     double mp = shfl(m, base + OFF + p);
-    double r2 = dx[0] * dx[0];
+    double r2 = kmul(k, dx[0], dx[0]);
     r2 = fma(dx[1], dx[1], r2);
     r2 = fma(dx[2], dx[2], r2);
     double rho = rsqrt(r2);
-    double sp = mp * (rho * rho * rho);
+    double sp = kmul(k, mp, kmul(k, kmul(k, rho, rho), rho));
 #pragma unroll
     for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
     d2[ARing<M>::RT - 1] = r2;
@@ -163,17 +163,17 @@ struct ChiState {
 // first step of a call: Vallado's guess).  Executed by every lane of the warp; lanes with
 // `on` false do not change their state.  Returns false on non-convergence in 50
 // iterations.
-static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, double (&r)[3], double (&v)[3], double h,
-                                                 ChiState &cs, int &iters) {
-  const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const KepConst &K, double (&r)[3], double (&v)[3],
+                                                 double h, ChiState &cs, int &iters) {
+  const double r2 = fma(r[2], r[2], fma(r[1], r[1], kmul(k, r[0], r[0])));
   const double rinv0 = rsqrt(r2);
-  const double r0 = r2 * rinv0;
-  const double sig0 = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
-  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-  const double alpha = fma(-v2, K.muinv, 2.0 * rinv0);
-  const double s0 = sig0 * K.smuinv;
+  const double r0 = kmul(k, r2, rinv0);
+  const double sig0 = fma(r[2], v[2], fma(r[1], v[1], kmul(k, r[0], v[0])));
+  const double v2 = fma(v[2], v[2], fma(v[1], v[1], kmul(k, v[0], v[0])));
+  const double alpha = fma(-v2, K.muinv, kmul(k, 2.0, rinv0));
+  const double s0 = kmul(k, sig0, K.smuinv);
   const double beta = fma(-alpha, r0, 1.0);
-  const double target = K.smu * h;
+  const double target = kmul(k, K.smu, h);
   double x = cs.n >= 2 ? 2.0 * cs.chi - cs.prev : cs.chi;
   if (on && cs.n == 0) x = chi_guess(K, r, v, r0, sig0, alpha, h);
   bool done = !on;
@@ -186,29 +186,31 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   for (int i = 0; i < 50; i++) {
     if (__all_sync(0xffffffffu, done)) break;
     if (!done) {
-      const double x2 = x * x;
-      const double z = alpha * x2;
+      const double x2 = kmul(k, x, x);
+      const double z = kmul(k, alpha, x2);
       double c2, c3;
       stumpff23(z, c2, c3);
       U0 = fma(-z, c2, 1.0);
-      U1 = x * fma(-z, c3, 1.0);
-      U2 = x2 * c2;
-      U3 = x2 * x * c3;
+      U1 = kmul(k, x, fma(-z, c3, 1.0));
+      U2 = kmul(k, x2, c2);
+      U3 = kmul(k, kmul(k, x2, x), c3);
       const double F = fma(s0, U2, fma(beta, U3, fma(r0, x, -target)));
       const double dF = fma(s0, U1, fma(beta, U2, r0));  // |r(chi)|
-      const double ddF = fma(s0, U0, beta * U1);
+      const double ddF = fma(s0, U0, kmul(k, beta, U1));
       dx = F / dF;
-      x -= dx;
+      x = ksub(k, x, dx);
       it++;
-      if (fabs(dx) <= 1e-14 * fmax(1.0, fabs(x)) || fabs(ddF) * (dx * dx) <= 2e-16 * fabs(x) * fabs(dF)) done = true;
+      if (fabs(dx) <= kmul(k, 1e-14, fmax(1.0, fabs(x))) ||
+          kmul(k, fabs(ddF), kmul(k, dx, dx)) <= kmul(k, kmul(k, 2e-16, fabs(x)), fabs(dF)))
+        done = true;
     }
   }
   iters = it;
   if (!on) return true;
   if (!done) return false;
   if (fabs(dx) <= 1e-6 * fmax(1.0, fabs(x))) {
-    const double d2h = 0.5 * dx * dx;
-    const double U1n = fma(-alpha * U1, d2h, fma(-U0, dx, U1));
+    const double d2h = kmul(k, kmul(k, 0.5, dx), dx);
+    const double U1n = fma(kmul(k, -alpha, U1), d2h, fma(-U0, dx, U1));
     const double U2n = fma(U0, d2h, fma(-U1, dx, U2));
     U3 = fma(U1, d2h, fma(-U2, dx, U3));
     U1 = U1n;
@@ -226,13 +228,13 @@ static __device__ __noinline__ bool kepler_drift(bool on, const KepConst &K, dou
   const double g = fma(-U3, K.smuinv, h);
   double rn[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], g * v[c]);
-  const double rinv = rsqrt(rn[0] * rn[0] + rn[1] * rn[1] + rn[2] * rn[2]);
-  const double fd = -K.smu * U1 * (rinv0 * rinv);
+  for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], kmul(k, g, v[c]));
+  const double rinv = rsqrt(fma(rn[2], rn[2], fma(rn[1], rn[1], kmul(k, rn[0], rn[0]))));
+  const double fd = kmul(k, kmul(k, -K.smu, U1), kmul(k, rinv0, rinv));
   const double gd = fma(-U2, rinv, 1.0);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    v[c] = fma(fd, r[c], gd * v[c]);
+    v[c] = fma(fd, r[c], kmul(k, gd, v[c]));
     r[c] = rn[c];
   }
   cs.prev = cs.chi;
@@ -306,37 +308,37 @@ __device__ __forceinline__ void from_jacobi(const double (&q)[3], const double (
 
 // heliocentric positions from Jacobi ones: Q_b = r'_b + sum_{1<=k<b} w_k r'_k, Q_0 = 0
 template <int N>
-__device__ __forceinline__ void jacobi_helio(const double (&q)[3], double w, int b, double (&Q)[3]) {
+__device__ __forceinline__ void jacobi_helio(const F64k &k, const double (&q)[3], double w, int b, double (&Q)[3]) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    double pre = grp_scan_excl<N>(b == 0 ? 0.0 : w * q[c], b);
-    Q[c] = b == 0 ? 0.0 : q[c] + pre;
+    double pre = grp_scan_excl<N>(k, b == 0 ? 0.0 : kmul(k, w, q[c]), b);
+    Q[c] = b == 0 ? 0.0 : kadd(k, q[c], pre);
   }
 }
 
 // Interaction acceleration.  DH: planet-planet terms (Sec. 2.2.3).  Jacobi: Jacobi
 // components of all pair accelerations plus mu_b r'_b/|r'_b|^3.
 template <int N, bool JAC>
-__device__ __forceinline__ void mvs_acc(const double (&q)[3], double m, double w, double eta_prev_inv, double mu,
+__device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], double m, double w, double eta_prev_inv, double mu,
                                         int b, int base, double (&acc)[3], double (&Q)[3],
                                         double (&d2)[ARing<(JAC ? N : N - 1)>::RTA]) {
   if constexpr (!JAC) {
-    ring_acc<N - 1, 1>(q, m, b == 0 ? 0 : b - 1, base, acc, d2);
+    ring_acc<N - 1, 1>(fk, q, m, b == 0 ? 0 : b - 1, base, acc, d2);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       if (b == 0) acc[c] = 0.0;
       Q[c] = q[c];
     }
   } else {
-    jacobi_helio<N>(q, w, b, Q);
+    jacobi_helio<N>(fk, q, w, b, Q);
     double a[3];
-    ring_acc<N, 0>(Q, m, b, base, a, d2);
-    const double r2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
+    const double r2 = fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0])));
     const double rho = rsqrt(r2);
-    const double k = mu * rho * rho * rho;
+    const double k = kmul(fk, kmul(fk, kmul(fk, mu, rho), rho), rho);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      double pre = grp_scan_excl<N>(m * a[c], b);
+      double pre = grp_scan_excl<N>(fk, kmul(fk, m, a[c]), b);
       acc[c] = b == 0 ? 0.0 : fma(-pre, eta_prev_inv, fma(k, q[c], a[c]));
     }
   }
@@ -414,7 +416,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
   double acc[3], Q[3], d2[RTA];
 #pragma unroll
   for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-  mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+  mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
 
   bool alive = runnable;
   int steps_done = 0;
@@ -431,8 +433,8 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
       // Cartesian drift half step: CoM by v_cm, planets by the star's reflex sum m_j u_j / m0
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
       }
     } else {
 #pragma unroll
@@ -444,17 +446,17 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     // Keplerian drift of every planet
     int its = 0;
-    bool ok = kepler_drift(active && b != 0, K, q, u, h, cs, its);
+    bool ok = kepler_drift(P.fk, active && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
     // accelerations at the new positions, reused by the next step's first kick
-    mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+    mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     if (!JAC) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
         Q[c] = q[c];
       }
     }
@@ -469,7 +471,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
       steps_done = k;
     }
     // monitor on the heliocentric positions at the end of the step
-    const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    const double q2 = fma(Q[2], Q[2], fma(Q[1], Q[1], kmul(P.fk, Q[0], Q[0])));
     const bool nf = nonfinite(q[0]) | nonfinite(q[1]) | nonfinite(q[2]) | nonfinite(u[0]) | nonfinite(u[1]) |
                     nonfinite(u[2]);
     const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
@@ -481,7 +483,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
         int p = jm + r;
         if (p >= MR) p -= MR;
         double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
-        if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+        if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
       }
     }
     const unsigned gm = ((1u << N) - 1u) << base;
@@ -649,7 +651,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       double an[3], Qn[3], d2n[RTA];
 #pragma unroll
       for (int r = 0; r < RTA; r++) d2n[r] = 0.0;
-      mvs_acc<N, JAC>(qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n);
+      mvs_acc<N, JAC>(P.fk, qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n);
       if (take) {
         s = ss;
         const double tn = B.t[s];
@@ -679,8 +681,8 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
     if (!JAC) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
       }
     } else {
 #pragma unroll
@@ -690,24 +692,24 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(active && b != 0, K, q, u, h, cs, its);
+    const bool ok = kepler_drift(P.fk, active && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
     double Q[3], d2[RTA];
 #pragma unroll
     for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-    mvs_acc<N, JAC>(q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+    mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     if (!JAC) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(b == 0 ? 0.0 : m * u[c], b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(hh * m0inv, ps, q[c]);
+        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
+        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
         Q[c] = q[c];
       }
     }
     // monitor on the heliocentric positions at the end of the step
-    const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+    const double q2 = fma(Q[2], Q[2], fma(Q[1], Q[1], kmul(P.fk, Q[0], Q[0])));
     const bool nf = nonfinite(q[0]) | nonfinite(q[1]) | nonfinite(q[2]) | nonfinite(u[0]) | nonfinite(u[1]) |
                     nonfinite(u[2]);
     const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
@@ -719,7 +721,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
         int p = jm + r;
         if (p >= MR) p -= MR;
         double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
-        if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+        if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
       }
     }
     const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;

@@ -24,7 +24,7 @@ __device__ __forceinline__ double warp_scan_excl(double v, int lane) {
 // Acceleration ring over M members at lanes OFF..OFF+M-1 (member j); lanes outside the
 // members mirror member 0 and their results are discarded.  Round r's squared pair
 // distance goes to d2s[(r - 1) * 32 + lane].
-__device__ __forceinline__ void wring_acc_members(const double (&x)[3], double m, int j, int M, int OFF,
+__device__ __forceinline__ void wring_acc_members(const F64k &k, const double (&x)[3], double m, int j, int M, int OFF,
                                                   double (&a)[3], double *d2s, int lane) {
   const int RF = (M - 1) / 2, RT = RF + ((M & 1) ? 0 : 1);
 #pragma unroll
@@ -39,18 +39,18 @@ __device__ __forceinline__ void wring_acc_members(const double (&x)[3], double m
     if (q < 0) q += M;
     double dx[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) dx[c] = shfl(x[c], OFF + p) - x[c];
+    for (int c = 0; c < 3; c++) dx[c] = ksub(k, shfl(x[c], OFF + p), x[c]);
     const double mp = shfl(m, OFF + p);
-    double r2 = dx[0] * dx[0];
+    double r2 = kmul(k, dx[0], dx[0]);
     r2 = fma(dx[1], dx[1], r2);
     r2 = fma(dx[2], dx[2], r2);
     const double rho = rsqrt(r2);
-    const double rho3 = rho * rho * rho;
-    const double sp = mp * rho3;
+    const double rho3 = kmul(k, kmul(k, rho, rho), rho);
+    const double sp = kmul(k, mp, rho3);
 #pragma unroll
     for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
     if (full) {
-      const double si = m * rho3;
+      const double si = kmul(k, m, rho3);
       double rdx[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) rdx[c] = shfl(dx[c], OFF + q);
@@ -131,10 +131,10 @@ __device__ __forceinline__ void wide_to_inertial(const double (&q)[3], const dou
 
 // interaction acceleration (see mvs_acc) and heliocentric positions Q for the monitor
 template <bool JAC>
-__device__ __forceinline__ void wide_mvs_acc(const double (&q)[3], const WideMass &W, int b, int n, bool real,
+__device__ __forceinline__ void wide_mvs_acc(const F64k &fk, const double (&q)[3], const WideMass &W, int b, int n, bool real,
                                              int lane, double (&acc)[3], double (&Q)[3], double *d2s) {
   if (!JAC) {
-    wring_acc_members(q, W.m, b == 0 ? 0 : b - 1, n - 1, 1, acc, d2s, lane);
+    wring_acc_members(fk, q, W.m, b == 0 ? 0 : b - 1, n - 1, 1, acc, d2s, lane);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       if (b == 0) acc[c] = 0.0;
@@ -147,10 +147,10 @@ __device__ __forceinline__ void wide_mvs_acc(const double (&q)[3], const WideMas
       Q[c] = b == 0 ? 0.0 : q[c] + pre;
     }
     double a[3];
-    wring_acc_members(Q, W.m, b, n, 0, a, d2s, lane);
-    const double r2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    wring_acc_members(fk, Q, W.m, b, n, 0, a, d2s, lane);
+    const double r2 = fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0])));
     const double rho = rsqrt(r2);
-    const double k = W.mu * rho * rho * rho;
+    const double k = kmul(fk, kmul(fk, kmul(fk, W.mu, rho), rho), rho);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const double pre = warp_scan_excl(real ? W.m * a[c] : 0.0, lane);
@@ -201,7 +201,7 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
   }
   double q[3], u[3], acc[3], Q[3];
   wide_to_canonical<JAC>(x, v, W, b, real, lane, q, u);
-  wide_mvs_acc<JAC>(q, W, b, n, real, lane, acc, Q, d2s);
+  wide_mvs_acc<JAC>(P.fk, q, W, b, n, real, lane, acc, Q, d2s);
   ChiState cs;
   unsigned long long kep_iters = 0;
   int steps = 0, code = 0;
@@ -222,9 +222,9 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(real && b != 0, K, q, u, h, cs, its);
+    const bool ok = kepler_drift(P.fk, real && b != 0, K, q, u, h, cs, its);
     kep_iters += its;
-    wide_mvs_acc<JAC>(q, W, b, n, real, lane, acc, Q, d2s);
+    wide_mvs_acc<JAC>(P.fk, q, W, b, n, real, lane, acc, Q, d2s);
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     if (!JAC) {
@@ -249,7 +249,7 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
       if (p >= MR) p -= MR;
       const double q2p = shfl(q2, OFF + p);
       const double kc = kcs[(r - 1) * 32 + lane];
-      if (kc > 0.0 && close_encounter(d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
+      if (kc > 0.0 && close_encounter(P.fk, d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
     }
     const unsigned bnf = __ballot_sync(FULL, nf) & gm;
     const unsigned bkn = __ballot_sync(FULL, !ok) & gm;

@@ -63,7 +63,7 @@ __device__ __forceinline__ double rk_err2(double px, double pv, double X2, doubl
 // One Cash-Karp step of length h from (x, v) with first-stage acceleration a1: writes
 // the 5th-order solution and, when E is true, the error vector (5th minus 4th order).
 template <int N, bool E>
-__device__ __forceinline__ void rkck_stages(const double (&x)[3], const double (&v)[3], const double (&a1)[3],
+__device__ __forceinline__ void rkck_stages(const F64k &k, const double (&x)[3], const double (&v)[3], const double (&a1)[3],
                                             double m, int b, int base, double h, double (&x5)[3], double (&v5)[3],
                                             double (&ex)[3], double (&ev)[3]) {
   constexpr int RT = ARing<N>::RTA;
@@ -73,43 +73,43 @@ __device__ __forceinline__ void rkck_stages(const double (&x)[3], const double (
   double xs[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, CK::A21 * v[c], x[c]);
-    v2[c] = fma(h, CK::A21 * a1[c], v[c]);
+    xs[c] = fma(h, kmul(k, CK::A21, v[c]), x[c]);
+    v2[c] = fma(h, kmul(k, CK::A21, a1[c]), v[c]);
   }
-  ring_acc<N, 0>(xs, m, b, base, a2, d2);
+  ring_acc<N, 0>(k, xs, m, b, base, a2, d2);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A32, v2[c], CK::A31 * v[c]), x[c]);
-    v3[c] = fma(h, fma(CK::A32, a2[c], CK::A31 * a1[c]), v[c]);
+    xs[c] = fma(h, fma(CK::A32, v2[c], kmul(k, CK::A31, v[c])), x[c]);
+    v3[c] = fma(h, fma(CK::A32, a2[c], kmul(k, CK::A31, a1[c])), v[c]);
   }
-  ring_acc<N, 0>(xs, m, b, base, a3, d2);
+  ring_acc<N, 0>(k, xs, m, b, base, a3, d2);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], CK::A41 * v[c])), x[c]);
-    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], CK::A41 * a1[c])), v[c]);
+    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], kmul(k, CK::A41, v[c]))), x[c]);
+    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], kmul(k, CK::A41, a1[c]))), v[c]);
   }
-  ring_acc<N, 0>(xs, m, b, base, a4, d2);
+  ring_acc<N, 0>(k, xs, m, b, base, a4, d2);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], CK::A51 * v[c]))), x[c]);
-    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], CK::A51 * a1[c]))), v[c]);
+    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], kmul(k, CK::A51, v[c])))), x[c]);
+    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], kmul(k, CK::A51, a1[c])))), v[c]);
   }
-  ring_acc<N, 0>(xs, m, b, base, a5, d2);
+  ring_acc<N, 0>(k, xs, m, b, base, a5, d2);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], CK::A61 * v[c])))),
+    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], kmul(k, CK::A61, v[c]))))),
                 x[c]);
-    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], CK::A61 * a1[c])))),
+    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], kmul(k, CK::A61, a1[c]))))),
                 v[c]);
   }
-  ring_acc<N, 0>(xs, m, b, base, a6, d2);
+  ring_acc<N, 0>(k, xs, m, b, base, a6, d2);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], CK::B1 * v[c]))), x[c]);
-    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], CK::B1 * a1[c]))), v[c]);
+    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], kmul(k, CK::B1, v[c])))), x[c]);
+    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], kmul(k, CK::B1, a1[c])))), v[c]);
     if (E) {
-      ex[c] = h * fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], CK::E1 * v[c]))));
-      ev[c] = h * fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], CK::E1 * a1[c]))));
+      ex[c] = kmul(k, h, fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], kmul(k, CK::E1, v[c]))))));
+      ev[c] = kmul(k, h, fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], kmul(k, CK::E1, a1[c]))))));
     }
   }
 }
@@ -188,7 +188,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
         if (take) kc[r - 1] = k;
       }
       double an[3], d2[RT];
-      ring_acc<N, 0>(x, m, b, base, an, d2);
+      ring_acc<N, 0>(P.fk, x, m, b, base, an, d2);
       if (take) {
 #pragma unroll
         for (int c = 0; c < 3; c++) a1[c] = an[c];
@@ -227,7 +227,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
       hs = (last ? rem : h) * dir;
     }
     double x5[3], v5[3], ex[3], ev[3];
-    rkck_stages<N, ADAPT>(x, v, a1, m, b, base, hs, x5, v5, ex, ev);
+    rkck_stages<N, ADAPT>(P.fk, x, v, a1, m, b, base, hs, x5, v5, ex, ev);
     bool accept = alive;
     double err = 0.0;  // adaptive: the squared scaled error of the trial
     bool bad = false;
@@ -245,7 +245,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
 #pragma unroll
     for (int c = 0; c < 3; c++) xn[c] = accept ? x5[c] : x[c];
     double an[3], d2[RT];
-    ring_acc<N, 0>(xn, m, b, base, an, d2);
+    ring_acc<N, 0>(P.fk, xn, m, b, base, an, d2);
     if (accept) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -267,7 +267,7 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
       int p = b + r;
       if (p >= N) p -= N;
       double q2p = shfl(q2, base + p);
-      if (kc[r - 1] > 0.0 && close_encounter(d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
+      if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
     }
     const unsigned bnf = __ballot_sync(FULL, (accept && nf) || (alive && bad)) & gm;
     const unsigned bej = __ballot_sync(FULL, accept && ej) & gm;

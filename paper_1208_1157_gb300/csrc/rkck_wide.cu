@@ -9,7 +9,7 @@ namespace swarm {
 
 // one step of length h from (x, v) with first-stage acceleration a1 (see rkck_stages)
 template <bool E>
-__device__ __forceinline__ void wide_rkck_stages(const double (&x)[3], const double (&v)[3], const double (&a1)[3],
+__device__ __forceinline__ void wide_rkck_stages(const F64k &k, const double (&x)[3], const double (&v)[3], const double (&a1)[3],
                                                  double m, int b, const WideRing &R, double h, double (&x5)[3],
                                                  double (&v5)[3], double (&ex)[3], double (&ev)[3], double *d2s,
                                                  int lane) {
@@ -18,43 +18,43 @@ __device__ __forceinline__ void wide_rkck_stages(const double (&x)[3], const dou
   double xs[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, CK::A21 * v[c], x[c]);
-    v2[c] = fma(h, CK::A21 * a1[c], v[c]);
+    xs[c] = fma(h, kmul(k, CK::A21, v[c]), x[c]);
+    v2[c] = fma(h, kmul(k, CK::A21, a1[c]), v[c]);
   }
-  wring_acc(xs, m, b, R, a2, d2s, lane);
+  wring_acc(k, xs, m, b, R, a2, d2s, lane);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A32, v2[c], CK::A31 * v[c]), x[c]);
-    v3[c] = fma(h, fma(CK::A32, a2[c], CK::A31 * a1[c]), v[c]);
+    xs[c] = fma(h, fma(CK::A32, v2[c], kmul(k, CK::A31, v[c])), x[c]);
+    v3[c] = fma(h, fma(CK::A32, a2[c], kmul(k, CK::A31, a1[c])), v[c]);
   }
-  wring_acc(xs, m, b, R, a3, d2s, lane);
+  wring_acc(k, xs, m, b, R, a3, d2s, lane);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], CK::A41 * v[c])), x[c]);
-    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], CK::A41 * a1[c])), v[c]);
+    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], kmul(k, CK::A41, v[c]))), x[c]);
+    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], kmul(k, CK::A41, a1[c]))), v[c]);
   }
-  wring_acc(xs, m, b, R, a4, d2s, lane);
+  wring_acc(k, xs, m, b, R, a4, d2s, lane);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], CK::A51 * v[c]))), x[c]);
-    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], CK::A51 * a1[c]))), v[c]);
+    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], kmul(k, CK::A51, v[c])))), x[c]);
+    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], kmul(k, CK::A51, a1[c])))), v[c]);
   }
-  wring_acc(xs, m, b, R, a5, d2s, lane);
+  wring_acc(k, xs, m, b, R, a5, d2s, lane);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], CK::A61 * v[c])))),
+    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], kmul(k, CK::A61, v[c]))))),
                 x[c]);
-    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], CK::A61 * a1[c])))),
+    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], kmul(k, CK::A61, a1[c]))))),
                 v[c]);
   }
-  wring_acc(xs, m, b, R, a6, d2s, lane);
+  wring_acc(k, xs, m, b, R, a6, d2s, lane);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], CK::B1 * v[c]))), x[c]);
-    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], CK::B1 * a1[c]))), v[c]);
+    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], kmul(k, CK::B1, v[c])))), x[c]);
+    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], kmul(k, CK::B1, a1[c])))), v[c]);
     if (E) {
-      ex[c] = h * fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], CK::E1 * v[c]))));
-      ev[c] = h * fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], CK::E1 * a1[c]))));
+      ex[c] = kmul(k, h, fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], kmul(k, CK::E1, v[c]))))));
+      ev[c] = kmul(k, h, fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], kmul(k, CK::E1, a1[c]))))));
     }
   }
 }
@@ -109,7 +109,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
     kcs[(r - 1) * 32 + lane] = (real && b != 0 && p != 0) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
   }
   double a1[3];
-  wring_acc(x, m, b, R, a1, d2s, lane);
+  wring_acc(P.fk, x, m, b, R, a1, d2s, lane);
   double t = t0, h = fabs(P.dt);
   const double inv_eps2 = 1.0 / (P.rk_eps * P.rk_eps);
   int steps = 0, trials = 0, code = 0;
@@ -126,7 +126,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
       hs = (last ? rem : h) * dir;
     }
     double x5[3], v5[3], ex[3], ev[3];
-    wide_rkck_stages<ADAPT>(x, v, a1, m, b, R, hs, x5, v5, ex, ev, d2s, lane);
+    wide_rkck_stages<ADAPT>(P.fk, x, v, a1, m, b, R, hs, x5, v5, ex, ev, d2s, lane);
     bool accept = true, bad = false;
     double err = 0.0;
     if (ADAPT) {
@@ -143,7 +143,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
 #pragma unroll
     for (int c = 0; c < 3; c++) xn[c] = accept ? x5[c] : x[c];
     double an[3];
-    wring_acc(xn, m, b, R, an, d2s, lane);
+    wring_acc(P.fk, xn, m, b, R, an, d2s, lane);
     if (accept) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -167,7 +167,7 @@ __device__ __forceinline__ void wide_rkck_body(const BinView &B, const StepParam
       if (p >= n) p -= n;
       const double q2p = shfl(q2, p);
       const double kc = kcs[(r - 1) * 32 + lane];
-      if (kc > 0.0 && close_encounter(d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
+      if (kc > 0.0 && close_encounter(P.fk, d2s[(r - 1) * 32 + lane], kc, q2, q2p)) ce = true;
     }
     const unsigned bnf = __ballot_sync(FULL, (accept && nf) || bad) & gm;
     const unsigned bej = __ballot_sync(FULL, accept && ej) & gm;
