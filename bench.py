@@ -45,15 +45,21 @@ def log(*a):
 
 # ------------------------------------------------------------------ operation counts
 def hermite_flops_per_system_step(n, n_corr=2):
-    """FP64 operations of the implemented Hermite step (a DFMA counts 2, rsqrt 1).
+    """FP64 operations of the implemented Hermite step, system per lane (a DFMA counts 2,
+    rsqrt 1).  The step runs on coordinates relative to body 0 plus the barycentre.
 
-    per unique pair and evaluation: 6 differences, 2 dot products (2 x 5), rsqrt (1),
-    rho^2, rho^3 (2), -3 (r.u) rho^2 (2), w = dv + c dx (3 DFMA = 6), each body's share
-    (1 DMUL + 6 DFMA = 13, twice) = 53; n_corr + 1 evaluations per step.
-    per body component and step: predictor 5 DFMA, corrector bases 4 DFMA, 4 DFMA per
-    corrector pass: (9 + 4 n_corr) * 2 flops."""
-    P = n * (n - 1) // 2
-    return (n_corr + 1) * P * 53 + 3 * n * (9 + 4 * n_corr) * 2
+    per evaluation (n_corr + 1 per step):
+      each body k >= 1 with body 0: |X|^2, X.V (2 x 5), rsqrt (1), rho^2, rho^3 (2),
+        -3 (X.V) rho^2 (2), m_k s, m_0 s (2), w = V + c X (6), the bases of A_k and J_k
+        (2 x 3 DFMA = 12): 35;
+      the sums m_j s_j X_j and m_j s_j w_j over k >= 1: 6 + 12 (n - 2);
+      each pair of bodies i, k >= 1: 6 differences, 2 dot products (10), rsqrt (1),
+        rho^2, rho^3 (2), -3 (r.u) rho^2 (2), w (6), each body's share (1 + 12, twice) = 53;
+    per component of bodies k >= 1 and step: predictor 5 DFMA, corrector bases 4 DFMA,
+      4 DFMA per corrector pass: (9 + 4 n_corr) * 2; the barycentre's drift 3 DFMA = 6."""
+    P = (n - 1) * (n - 2) // 2
+    per_eval = 35 * (n - 1) + 6 + 12 * (n - 2) + 53 * P
+    return (n_corr + 1) * per_eval + 3 * (n - 1) * (9 + 4 * n_corr) * 2 + 6
 
 
 def source_hash(patterns):

@@ -313,6 +313,120 @@ __device__ __forceinline__ void spl_accjerk(const F64k &kk, const double (&x)[N]
   }
 }
 
+// Coordinates relative to body 0 (k >= 1, in place) and the barycentre of the system, and
+// back: x_0 = X_cm - sum_{k>=1} m_k X_k / M, x_k = X_k + x_0 (likewise v).
+template <int N>
+__device__ __forceinline__ void spl_to_rel(const double (&m)[N], double (&x)[N][3], double (&v)[N][3], double &Minv,
+                                           double (&Xc)[3], double (&Vc)[3]) {
+  double Mt = m[0];
+#pragma unroll
+  for (int i = 1; i < N; i++) Mt += m[i];
+  Minv = 1.0 / Mt;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double sx = m[0] * x[0][c], sv = m[0] * v[0][c];
+#pragma unroll
+    for (int i = 1; i < N; i++) {
+      sx = fma(m[i], x[i][c], sx);
+      sv = fma(m[i], v[i][c], sv);
+    }
+    Xc[c] = sx * Minv;
+    Vc[c] = sv * Minv;
+#pragma unroll
+    for (int k = 1; k < N; k++) {
+      x[k][c] -= x[0][c];
+      v[k][c] -= v[0][c];
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void spl_from_rel(const double (&m)[N], const double (&x)[N][3], const double (&v)[N][3],
+                                             double Minv, const double (&Xc)[3], const double (&Vc)[3],
+                                             double (&xo)[N][3], double (&vo)[N][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double sx = 0.0, sv = 0.0;
+#pragma unroll
+    for (int k = 1; k < N; k++) {
+      sx = fma(m[k], x[k][c], sx);
+      sv = fma(m[k], v[k][c], sv);
+    }
+    const double x0 = fma(-sx, Minv, Xc[c]), v0 = fma(-sv, Minv, Vc[c]);
+    xo[0][c] = x0;
+    vo[0][c] = v0;
+#pragma unroll
+    for (int k = 1; k < N; k++) {
+      xo[k][c] = x[k][c] + x0;
+      vo[k][c] = v[k][c] + v0;
+    }
+  }
+}
+
+// Acceleration and jerk of bodies k = 1..N-1 relative to body 0 (index 0: body 0 itself), from
+// the coordinates X_k = x_k - x_0, V_k = v_k - v_0 (Eq. 1 and its time derivative):
+//   A_k = a_k - a_0 = -m_0 s_k X_k - I + sum_{i >= 1, i != k} m_i s_ik (X_i - X_k),
+//   I = a_0 = sum_{j >= 1} m_j s_j X_j,   s = 1/r^3,
+// and J_k likewise with the jerk vectors w of the pairs; A[0], J[0] receive body 0's own
+// acceleration and jerk, I and its jerk counterpart.  Monitor distances:
+// q2[k] = |X_k|^2, d2[i][k] = |X_k - X_i|^2.
+template <int N>
+__device__ __forceinline__ void spl_accjerk_rel(const F64k &kk, const double (&X)[N][3], const double (&V)[N][3],
+                                                const double (&m)[N], double (&A)[N][3], double (&J)[N][3],
+                                                double (&q2)[N], double (&d2)[N][N]) {
+  double w0[N][3], m0s[N], IA[3], IJ[3];
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    double r2 = kmul(kk, X[k][0], X[k][0]);
+    r2 = fma(X[k][1], X[k][1], r2);
+    r2 = fma(X[k][2], X[k][2], r2);
+    double rv = kmul(kk, X[k][0], V[k][0]);
+    rv = fma(X[k][1], V[k][1], rv);
+    rv = fma(X[k][2], V[k][2], rv);
+    const double rho = rsqrt(r2);
+    const double rho2 = kmul(kk, rho, rho);
+    const double s3 = kmul(kk, rho2, rho);
+    const double cc = kmul(kk, -3.0, kmul(kk, rv, rho2));
+    const double ms = kmul(kk, m[k], s3);
+    m0s[k] = kmul(kk, m[0], s3);
+    q2[k] = r2;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      w0[k][c] = fma(cc, X[k][c], V[k][c]);
+      IA[c] = k == 1 ? kmul(kk, ms, X[k][c]) : fma(ms, X[k][c], IA[c]);
+      IJ[c] = k == 1 ? kmul(kk, ms, w0[k][c]) : fma(ms, w0[k][c], IJ[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    A[0][c] = IA[c];
+    J[0][c] = IJ[c];
+  }
+#pragma unroll
+  for (int k = 1; k < N; k++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      A[k][c] = fma(-m0s[k], X[k][c], -IA[c]);
+      J[k][c] = fma(-m0s[k], w0[k][c], -IJ[c]);
+    }
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+      double dx[3], w[3], rho3, r2;
+      pair_geom(kk, X[i], V[i], X[k], V[k], dx, w, rho3, r2);
+      const double sk = kmul(kk, m[k], rho3), si = kmul(kk, m[i], rho3);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        A[i][c] = fma(sk, dx[c], A[i][c]);
+        J[i][c] = fma(sk, w[c], J[i][c]);
+        A[k][c] = fma(-si, dx[c], A[k][c]);
+        J[k][c] = fma(-si, w[c], J[k][c]);
+      }
+      d2[i][k] = r2;
+    }
+}
+
 template <int N>
 __device__ __forceinline__ void spl_energy(const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
                                            double (&out)[4]) {

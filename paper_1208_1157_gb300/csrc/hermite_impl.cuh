@@ -172,9 +172,17 @@ __device__ __forceinline__ void bpl_hermite_body(const BinView &B, const StepPar
 }
 
 // ---------------------------------------------------------------- system per lane
-// The corrector bases Xb, Vb of a step live in registers, or (sb != nullptr) in this
-// lane's column of shared memory (sb[k * 128], k < 6N), which frees 12N registers for a
-// build with more resident warps.
+// Each lane integrates one system in coordinates relative to body 0, X_k = x_k - x_0 and
+// V_k = v_k - v_0 (k >= 1), plus the uniform motion of the barycentre.  Every operation
+// of the Hermite step (Eqs. 3-4) is linear in (x, v, a, jerk) and A_k = a_k - a_0, so this
+// is the step of the inertial coordinates in exact arithmetic (the barycentre of the
+// inertial step moves by h v_cm, its accelerations summing to zero); it drops body 0's
+// predictor and corrector and the coordinate differences of body 0's pairs.  Inertial
+// coordinates are rebuilt at log points and at the end:
+//   x_0 = X_cm - sum_{k>=1} m_k X_k / M,  x_k = X_k + x_0   (likewise v).
+// The corrector bases of a step live in registers, or (sb != nullptr) in this lane's
+// column of shared memory (sb[k * 128], k < 6N), which frees registers for a build with
+// more resident warps.
 template <int N>
 __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepParams &P, int unit,
                                                  double *sb = nullptr) {
@@ -206,8 +214,13 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 #pragma unroll
     for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
 
+  // relative coordinates (index 0 unused) and the barycentre
+  double Minv, Xc[3], Vc[3];
+  spl_to_rel<N>(m, x, v, Minv, Xc, Vc);
+  auto inertial = [&](double (&xo)[N][3], double (&vo)[N][3]) { spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo); };
+
   double a0[N][3], j0[N][3], q2[N], d2[N][N];
-  spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
+  spl_accjerk_rel<N>(P.fk, x, v, m, a0, j0, q2, d2);
   const HCoef cdt = hcoef(P.dt);
   const HCoef clast = hcoef(plan.h_last);
   int steps_done = 0;
@@ -219,7 +232,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     auto XB = [&](int i, int c) -> double & { return sb ? sb[(i * 3 + c) * 128] : Xr[i][c]; };
     auto VB = [&](int i, int c) -> double & { return sb ? sb[(3 * N + i * 3 + c) * 128] : Vr[i][c]; };
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
@@ -230,46 +243,48 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     if (printed) {
       PC = pcoef(C.h);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) XB(i, c) = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
     } else {
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) XB(i, c) = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
-      spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
+      spl_accjerk_rel<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], VB(i, c)));
       if (printed) {
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], XB(i, c)));
       } else {
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], XB(i, c)));
       }
     }
-    spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
+    spl_accjerk_rel<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         x[i][c] = xk[i][c];
         v[i][c] = vk[i][c];
       }
+#pragma unroll
+    for (int c = 0; c < 3; c++) Xc[c] = fma(C.h, Vc[c], Xc[c]);
     steps_done = k;
     bool nf = false, ej = false, ce = false;
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
 #pragma unroll
@@ -282,19 +297,24 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (code) break;
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
-      double e[4];
-      spl_energy<N>(x, v, m, e);
+      double xo[N][3], vo[N][3], e[4];
+      inertial(xo, vo);
+      spl_energy<N>(xo, vo, m, e);
       write_log(P, B.gidx[s], step_time(plan, k, t0, P.dt), e);
     }
   }
   const double tk = step_time(plan, steps_done, t0, P.dt);
+  {
+    double xo[N][3], vo[N][3];
+    inertial(xo, vo);
 #pragma unroll
-  for (int i = 0; i < N; i++)
+    for (int i = 0; i < N; i++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
-      B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
-    }
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + i) * SP + s] = xo[i][c];
+        B.v[(size_t)(c * N + i) * SP + s] = vo[i][c];
+      }
+  }
   B.t[s] = tk;
   B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
   if (P.counters) {
@@ -310,7 +330,8 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 // from the values at the start of the step, clamped so that the last step lands on the
 // system's end time.  P.dt carries tau (its sign gives the direction).  A launch takes at
 // most P.max_steps (or 2^24) steps per system; a system that has not reached its end time
-// then stays ACTIVE.
+// then stays ACTIVE.  The system-per-lane versions run on coordinates relative to body 0
+// like spl_hermite_body; Eq. 5 takes the inertial a and jerk rebuilt from them.
 constexpr int kAdaptiveStepCap = 1 << 24;
 
 __device__ __forceinline__ double adaptive_end(const BinView &B, const StepParams &P, int s) {
@@ -488,6 +509,24 @@ __device__ __forceinline__ double spl_eq5_sum(const double (&a)[N][3], const dou
   return num / den;
 }
 
+// The same sum from the relative-coordinate values of spl_accjerk_rel: a_0 = A[0],
+// a_k = A[k] + A[0] (likewise the jerks).
+template <int N>
+__device__ __forceinline__ double spl_eq5_sum_rel(const double (&A)[N][3], const double (&J)[N][3]) {
+  double a[N][3], j[N][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    a[0][c] = A[0][c];
+    j[0][c] = J[0][c];
+#pragma unroll
+    for (int k = 1; k < N; k++) {
+      a[k][c] = A[k][c] + A[0][c];
+      j[k][c] = J[k][c] + J[0][c];
+    }
+  }
+  return spl_eq5_sum<N>(a, j);
+}
+
 template <int N>
 __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, const StepParams &P, int unit) {
   const bool printed = P.corr_form != 0;  // warp-uniform
@@ -514,19 +553,21 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     B.status[s] = SWARM_SYS_DONE;
     return;
   }
+  double Minv, Xc[3], Vc[3];
+  spl_to_rel<N>(m, x, v, Minv, Xc, Vc);
   double kc[N][N];
 #pragma unroll
   for (int i = 1; i < N; i++)
 #pragma unroll
     for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
   double a0[N][3], j0[N][3], q2[N], d2[N][N];
-  spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
+  spl_accjerk_rel<N>(P.fk, x, v, m, a0, j0, q2, d2);
   const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
   double t = t0;
   int steps_done = 0, code = 0;
   bool reached = false;
   for (int k = 1; k <= cap; k++) {
-    double h = tau * rsqrt(spl_eq5_sum<N>(a0, j0));
+    double h = tau * rsqrt(spl_eq5_sum_rel<N>(a0, j0));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       break;
@@ -537,7 +578,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     const HCoef C = hcoef(h);
     double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
@@ -548,47 +589,49 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     if (printed) {
       PC = pcoef(C.h);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
     } else {
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
-      spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
+      spl_accjerk_rel<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
       if (printed) {
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
       } else {
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
       }
     }
-    spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
+    spl_accjerk_rel<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         x[i][c] = xk[i][c];
         v[i][c] = vk[i][c];
       }
+#pragma unroll
+    for (int c = 0; c < 3; c++) Xc[c] = fma(C.h, Vc[c], Xc[c]);
     steps_done = k;
     t = last ? te : t + h;
     bool nf = false, ej = false, ce = false;
 #pragma unroll
-    for (int i = 0; i < N; i++)
+    for (int i = 1; i < N; i++)
 #pragma unroll
       for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
 #pragma unroll
@@ -601,8 +644,9 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
     code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
     if (code) break;
     if (P.log_interval > 0 && (k % P.log_interval) == 0) {
-      double e[4];
-      spl_energy<N>(x, v, m, e);
+      double xo[N][3], vo[N][3], e[4];
+      spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
+      spl_energy<N>(xo, vo, m, e);
       write_log(P, B.gidx[s], t, e);
     }
     if (last) {
@@ -610,13 +654,17 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
       break;
     }
   }
+  {
+    double xo[N][3], vo[N][3];
+    spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
 #pragma unroll
-  for (int i = 0; i < N; i++)
+    for (int i = 0; i < N; i++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
-      B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
-    }
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + i) * SP + s] = xo[i][c];
+        B.v[(size_t)(c * N + i) * SP + s] = vo[i][c];
+      }
+  }
   B.t[s] = t;
   B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
   if (P.counters && steps_done > 0) {
@@ -639,6 +687,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
   const double tau = fabs(P.dt), dir = P.dt > 0 ? 1.0 : -1.0;
   const int cap = P.max_steps > 0 ? P.max_steps : kAdaptiveStepCap;
   double x[N][3], v[N][3], m[N], a0[N][3], j0[N][3], kc[N][N];
+  double Minv = 1.0, Xc[3] = {0.0, 0.0, 0.0}, Vc[3] = {0.0, 0.0, 0.0};
   double t = 0.0, te = 0.0;
   int s = 0, steps = 0;
   bool has = false, exhausted = false;
@@ -666,8 +715,9 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
           for (int i = 1; i < N; i++)
 #pragma unroll
             for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
+          spl_to_rel<N>(m, x, v, Minv, Xc, Vc);
           double q2[N], d2[N][N];
-          spl_accjerk<N>(P.fk, x, v, m, a0, j0, q2, d2);
+          spl_accjerk_rel<N>(P.fk, x, v, m, a0, j0, q2, d2);
           steps = 0;
           has = true;
         }
@@ -678,7 +728,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
     // one step (Eq. 5 length from the start-of-step a0, j0)
     int code = 0;
     bool finish = false, reached = false;
-    double h = tau * rsqrt(spl_eq5_sum<N>(a0, j0));
+    double h = tau * rsqrt(spl_eq5_sum_rel<N>(a0, j0));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       finish = true;
@@ -689,7 +739,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
       const HCoef C = hcoef(h);
       double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           xk[i][c] = fma(j0[i][c], C.h3_6, fma(a0[i][c], C.h2_2, fma(v[i][c], C.h, x[i][c])));
@@ -700,48 +750,50 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
       if (printed) {
         PC = pcoef(C.h);
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) Xb[i][c] = fma(j0[i][c], PC.pj, fma(a0[i][c], PC.pa, xk[i][c]));
       } else {
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) Xb[i][c] = fma(a0[i][c], C.h2_12, fma(v[i][c], C.hh, x[i][c]));
       }
       double q2[N], d2[N][N];
       for (int ic = 0; ic < P.n_corr; ic++) {
         double ak[N][3], jk[N][3];
-        spl_accjerk<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
+        spl_accjerk_rel<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
 #pragma unroll
-        for (int i = 0; i < N; i++)
+        for (int i = 1; i < N; i++)
 #pragma unroll
           for (int c = 0; c < 3; c++) vk[i][c] = fma(-C.h2_12, jk[i][c], fma(C.hh, ak[i][c], Vb[i][c]));
         if (printed) {
 #pragma unroll
-          for (int i = 0; i < N; i++)
+          for (int i = 1; i < N; i++)
 #pragma unroll
             for (int c = 0; c < 3; c++) xk[i][c] = fma(PC.cj, jk[i][c], fma(PC.ca, ak[i][c], Xb[i][c]));
         } else {
 #pragma unroll
-          for (int i = 0; i < N; i++)
+          for (int i = 1; i < N; i++)
 #pragma unroll
             for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], Xb[i][c]));
         }
       }
-      spl_accjerk<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
+      spl_accjerk_rel<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           x[i][c] = xk[i][c];
           v[i][c] = vk[i][c];
         }
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xc[c] = fma(C.h, Vc[c], Xc[c]);
       steps++;
       t = last ? te : t + h;
       bool nf = false, ej = false, ce = false;
 #pragma unroll
-      for (int i = 0; i < N; i++)
+      for (int i = 1; i < N; i++)
 #pragma unroll
         for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
 #pragma unroll
@@ -753,21 +805,26 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
           if (kc[i][k2] > 0.0 && close_encounter(P.fk, d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
       code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
       if (!code && P.log_interval > 0 && (steps % P.log_interval) == 0) {
-        double e[4];
-        spl_energy<N>(x, v, m, e);
+        double xo[N][3], vo[N][3], e[4];
+        spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
+        spl_energy<N>(xo, vo, m, e);
         write_log(P, B.gidx[s], t, e);
       }
       reached = last && !code;
       finish = code != 0 || last || steps >= cap;
     }
     if (finish) {
+      {
+        double xo[N][3], vo[N][3];
+        spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
 #pragma unroll
-      for (int i = 0; i < N; i++)
+        for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-          B.x[(size_t)(c * N + i) * SP + s] = x[i][c];
-          B.v[(size_t)(c * N + i) * SP + s] = v[i][c];
-        }
+          for (int c = 0; c < 3; c++) {
+            B.x[(size_t)(c * N + i) * SP + s] = xo[i][c];
+            B.v[(size_t)(c * N + i) * SP + s] = vo[i][c];
+          }
+      }
       B.t[s] = t;
       B.status[s] = code ? code : (reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
       if (P.counters && steps > 0) {

@@ -88,3 +88,27 @@ def test_mvs_chunked_launches(kind):
     assert np.array_equal(got["status"], ref["status"])
     ex, ev = per_system_errors(ens, got, ref)
     assert ex.max() <= 1e-10 and ev.max() <= 1e-10
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_mvs_backward_parity_and_return(kind):
+    # negative steps (t_end < t): parity with the oracle, and the symmetric map brought
+    # back to its start by the same number of steps of -dt
+    from paper_1208_1157_gb300 import swarm as S
+    from gpu_util import per_system_errors
+
+    ens = ics.mvs_compact(128, seed=15)
+    o = run_oracle(ens, -200 * DT, kind, -DT)
+    sens = oracle_sensitivity(ens, -200 * DT, kind, -DT)
+    g = run_gpu(ens, -200 * DT, kind, -DT)
+    assert_parity(ens, g, o, sens=sens, steps=200)
+    assert np.all(g["time"] == -200 * DT)
+    with S.Ensemble(ens) as e:
+        e.integrate(150 * DT, kind, DT)
+        e.integrate(0.0, kind, -DT)
+        back = e.state()
+    ex, ev = per_system_errors(ens, back, ens)
+    # round-off grows along the way and back like the oracle's own sensitivity
+    bound = np.maximum(1e-12, 30.0 * oracle_sensitivity(ens, 150 * DT, kind, DT))
+    assert np.all(ex <= bound) and np.all(ev <= bound)
+    assert np.all(back["time"] == 0.0)

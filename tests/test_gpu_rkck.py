@@ -112,3 +112,13 @@ def test_rkck_full_size_sampled():
     o = run_oracle(sub, TWO_PI, O.RKCK_ADAPTIVE, 0.05, ce=3.0, ej=100.0)
     sens = oracle_sensitivity(sub, TWO_PI, O.RKCK_ADAPTIVE, 0.05, ce=3.0, ej=100.0)
     assert_parity(sub, sample_rows(ens, g, idx), o, sens=sens, steps=1000, stop_time_rtol=1e-8)
+
+
+def test_rkck_fixed_backward_parity():
+    # negative fixed steps, ragged n with a shortened last step
+    ens = ics.ragged(200, seed=27)
+    t_end = -120.6 * DT
+    o = run_oracle(ens, t_end, O.RKCK, -DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, t_end, O.RKCK, -DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, t_end, RKCK, -DT, ce=3.0, ej=100.0)
+    assert_parity(ens, g, o, sens=sens, steps=121)
