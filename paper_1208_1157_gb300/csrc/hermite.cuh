@@ -25,6 +25,16 @@ __device__ __forceinline__ HCoef hcoef(double h) {
   c.h2_12 = h * h * (1.0 / 12.0);
   return c;
 }
+// the same coefficients with the products in DFMA form (steps chosen per step)
+__device__ __forceinline__ HCoef hcoef(const F64k &k, double h) {
+  HCoef c;
+  c.h = h;
+  c.h2_2 = kmul(k, kmul(k, 0.5, h), h);
+  c.h3_6 = kmul(k, kmul(k, c.h2_2, h), 1.0 / 3.0);
+  c.hh = kmul(k, 0.5, h);
+  c.h2_12 = kmul(k, kmul(k, h, h), 1.0 / 12.0);
+  return c;
+}
 // Printed-form corrector (Eq. 4 with 3/20 and the predicted base): its velocity update
 // equals the time-symmetric one, its position update is
 //   x_{k+1} = XP + (3/20) h^2 a_k - (1/30) h^3 j_k,  XP = x_p - (3/20) h^2 a0 - (7/60) h^3 j0.

@@ -396,11 +396,11 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
     const double ratio = (j0[0] * j0[0] + j0[1] * j0[1] + j0[2] * j0[2]) / (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
     const double ssum = grp_sum<N>(ratio, b, base);
     double h = tau * rsqrt(ssum);
-    const double rem = (te - t) * dir;
+    const double rem = kmul(P.fk, ksub(P.fk, te, t), dir);
     const bool last = h >= rem;
     const bool bad = !(h > 0.0) || nonfinite(h);
-    h = (last ? rem : h) * dir;
-    const HCoef C = hcoef(h);
+    h = kmul(P.fk, last ? rem : h, dir);
+    const HCoef C = hcoef(P.fk, h);
     double xk[3], vk[3], Xb[3], Vb[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -442,7 +442,7 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
         j0[c] = jn[c];
       }
       steps_done = k;
-      t = last ? te : t + h;
+      t = last ? te : kadd(P.fk, t, h);
     }
     const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
                     nonfinite(v[2]);
@@ -497,14 +497,14 @@ __device__ __forceinline__ void bpl_hermite_adaptive_body(const BinView &B, cons
 // one division: the running fraction num/den takes body i as (num A_i + J_i den)/(den A_i)
 // (A = |a|^2, J = |j|^2; den stays within range for the n <= 4 of this mapping).
 template <int N>
-__device__ __forceinline__ double spl_eq5_sum(const double (&a)[N][3], const double (&j)[N][3]) {
+__device__ __forceinline__ double spl_eq5_sum(const F64k &k, const double (&a)[N][3], const double (&j)[N][3]) {
   double num = 0.0, den = 1.0;
 #pragma unroll
   for (int i = 0; i < N; i++) {
-    const double A = fma(a[i][2], a[i][2], fma(a[i][1], a[i][1], a[i][0] * a[i][0]));
-    const double J = fma(j[i][2], j[i][2], fma(j[i][1], j[i][1], j[i][0] * j[i][0]));
-    num = fma(num, A, J * den);
-    den *= A;
+    const double A = fma(a[i][2], a[i][2], fma(a[i][1], a[i][1], kmul(k, a[i][0], a[i][0])));
+    const double J = fma(j[i][2], j[i][2], fma(j[i][1], j[i][1], kmul(k, j[i][0], j[i][0])));
+    num = fma(num, A, kmul(k, J, den));
+    den = kmul(k, den, A);
   }
   return num / den;
 }
@@ -512,7 +512,7 @@ __device__ __forceinline__ double spl_eq5_sum(const double (&a)[N][3], const dou
 // The same sum from the relative-coordinate values of spl_accjerk_rel: a_0 = A[0],
 // a_k = A[k] + A[0] (likewise the jerks).
 template <int N>
-__device__ __forceinline__ double spl_eq5_sum_rel(const double (&A)[N][3], const double (&J)[N][3]) {
+__device__ __forceinline__ double spl_eq5_sum_rel(const F64k &kk, const double (&A)[N][3], const double (&J)[N][3]) {
   double a[N][3], j[N][3];
 #pragma unroll
   for (int c = 0; c < 3; c++) {
@@ -520,11 +520,11 @@ __device__ __forceinline__ double spl_eq5_sum_rel(const double (&A)[N][3], const
     j[0][c] = J[0][c];
 #pragma unroll
     for (int k = 1; k < N; k++) {
-      a[k][c] = A[k][c] + A[0][c];
-      j[k][c] = J[k][c] + J[0][c];
+      a[k][c] = kadd(kk, A[k][c], A[0][c]);
+      j[k][c] = kadd(kk, J[k][c], J[0][c]);
     }
   }
-  return spl_eq5_sum<N>(a, j);
+  return spl_eq5_sum<N>(kk, a, j);
 }
 
 template <int N>
@@ -567,15 +567,15 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
   int steps_done = 0, code = 0;
   bool reached = false;
   for (int k = 1; k <= cap; k++) {
-    double h = tau * rsqrt(spl_eq5_sum_rel<N>(a0, j0));
+    double h = kmul(P.fk, tau, rsqrt(spl_eq5_sum_rel<N>(P.fk, a0, j0)));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       break;
     }
-    const double rem = (te - t) * dir;
+    const double rem = kmul(P.fk, ksub(P.fk, te, t), dir);
     const bool last = h >= rem;
-    h = (last ? rem : h) * dir;
-    const HCoef C = hcoef(h);
+    h = kmul(P.fk, last ? rem : h, dir);
+    const HCoef C = hcoef(P.fk, h);
     double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
 #pragma unroll
     for (int i = 1; i < N; i++)
@@ -628,7 +628,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_body(const BinView &B, cons
 #pragma unroll
     for (int c = 0; c < 3; c++) Xc[c] = fma(C.h, Vc[c], Xc[c]);
     steps_done = k;
-    t = last ? te : t + h;
+    t = last ? te : kadd(P.fk, t, h);
     bool nf = false, ej = false, ce = false;
 #pragma unroll
     for (int i = 1; i < N; i++)
@@ -728,15 +728,15 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
     // one step (Eq. 5 length from the start-of-step a0, j0)
     int code = 0;
     bool finish = false, reached = false;
-    double h = tau * rsqrt(spl_eq5_sum_rel<N>(a0, j0));
+    double h = kmul(P.fk, tau, rsqrt(spl_eq5_sum_rel<N>(P.fk, a0, j0)));
     if (!(h > 0.0) || nonfinite(h)) {
       code = SWARM_SYS_NONFINITE;
       finish = true;
     } else {
-      const double rem = (te - t) * dir;
+      const double rem = kmul(P.fk, ksub(P.fk, te, t), dir);
       const bool last = h >= rem;
-      h = (last ? rem : h) * dir;
-      const HCoef C = hcoef(h);
+      h = kmul(P.fk, last ? rem : h, dir);
+      const HCoef C = hcoef(P.fk, h);
       double xk[N][3], vk[N][3], Xb[N][3], Vb[N][3];
 #pragma unroll
       for (int i = 1; i < N; i++)
@@ -790,7 +790,7 @@ __device__ __forceinline__ void spl_hermite_adaptive_stream(const BinView &B, co
 #pragma unroll
       for (int c = 0; c < 3; c++) Xc[c] = fma(C.h, Vc[c], Xc[c]);
       steps++;
-      t = last ? te : t + h;
+      t = last ? te : kadd(P.fk, t, h);
       bool nf = false, ej = false, ce = false;
 #pragma unroll
       for (int i = 1; i < N; i++)
@@ -948,11 +948,11 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
       const double ratio = (j0[0] * j0[0] + j0[1] * j0[1] + j0[2] * j0[2]) / (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
       const double ssum = grp_sum<N>(ratio, b, base);
       h = tau * rsqrt(ssum);
-      const double rem = (te - t) * dir;
+      const double rem = kmul(P.fk, ksub(P.fk, te, t), dir);
       last = h >= rem;
       bad = !(h > 0.0) || nonfinite(h);
-      h = (last ? rem : h) * dir;
-      C = hcoef(h);
+      h = kmul(P.fk, last ? rem : h, dir);
+      C = hcoef(P.fk, h);
     }
     double xk[3], vk[3], Xb[3], Vb[3];
 #pragma unroll
@@ -996,7 +996,7 @@ __device__ __forceinline__ void bpl_hermite_stream(const BinView &B, const StepP
         j0[c] = jn[c];
       }
       steps++;
-      if (ADAPT) t = last ? te : t + h;
+      if (ADAPT) t = last ? te : kadd(P.fk, t, h);
     }
     const bool nf = nonfinite(x[0]) | nonfinite(x[1]) | nonfinite(x[2]) | nonfinite(v[0]) | nonfinite(v[1]) |
                     nonfinite(v[2]);
