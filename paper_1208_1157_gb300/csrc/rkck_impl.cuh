@@ -60,58 +60,74 @@ __device__ __forceinline__ double rk_err2(double px, double pv, double X2, doubl
   return fmax(px * (V2 * inv), pv * (X2 * inv)) * inv_eps2;
 }
 
+// The same stages in Nystrom form.  For y' = (v, a(x)) the stage positions need no stage
+// velocities: with v_j = v + h sum_l A_jl a_l,
+//   x_i = x + c_i h v + h^2 sum_l Abar_il a_l,     Abar = A A,  c_i = sum_j A_ij,
+//   x5  = x + h v + h^2 sum_l Bbar_l a_l,          Bbar = B5 A,
+//   ex  = h^2 sum_l Ebar_l a_l,                    Ebar = (B5 - B4) A  (sum_j E_j = 0),
+//   v5  = v + h sum_j B5_j a_j,   ev = h sum_j E_j a_j.
+// Exact rational products of the tableau above (Abar_32, Bbar_2, Bbar_6, Ebar_2 vanish).
+struct CKN {
+  static constexpr double C2 = 1.0 / 5.0, C3 = 3.0 / 10.0, C4 = 3.0 / 5.0, C6 = 7.0 / 8.0;
+  static constexpr double A31 = 9.0 / 200.0;
+  static constexpr double A41 = -9.0 / 100.0, A42 = 27.0 / 100.0;
+  static constexpr double A51 = 25.0 / 36.0, A52 = -7.0 / 4.0, A53 = 14.0 / 9.0;
+  static constexpr double A61 = 4949.0 / 27648.0, A62 = -805.0 / 4096.0, A63 = 8855.0 / 27648.0,
+                          A64 = 8855.0 / 110592.0;
+  static constexpr double B1 = 11.0 / 108.0, B3 = 50.0 / 189.0, B4 = 25.0 / 216.0, B5 = 1.0 / 56.0;
+  static constexpr double E1 = -277.0 / 73728.0, E3 = 1385.0 / 129024.0, E4 = -1385.0 / 147456.0,
+                          E5 = 277.0 / 114688.0;
+};
+
 // One Cash-Karp step of length h from (x, v) with first-stage acceleration a1: writes
 // the 5th-order solution and, when E is true, the error vector (5th minus 4th order).
+// acc(xs, a) evaluates the accelerations at the stage positions xs.
+template <bool E, class Acc>
+__device__ __forceinline__ void rkck_step(const F64k &k, const double (&x)[3], const double (&v)[3],
+                                          const double (&a1)[3], double h, Acc &&acc, double (&x5)[3],
+                                          double (&v5)[3], double (&ex)[3], double (&ev)[3]) {
+  double a2[3], a3[3], a4[3], a5[3], a6[3], xs[3];
+  const double h2 = kmul(k, h, h);
+  const double hc2 = kmul(k, CKN::C2, h), hc3 = kmul(k, CKN::C3, h), hc4 = kmul(k, CKN::C4, h),
+               hc6 = kmul(k, CKN::C6, h);
+#pragma unroll
+  for (int c = 0; c < 3; c++) xs[c] = fma(hc2, v[c], x[c]);
+  acc(xs, a2);
+#pragma unroll
+  for (int c = 0; c < 3; c++) xs[c] = fma(hc3, v[c], fma(h2, kmul(k, CKN::A31, a1[c]), x[c]));
+  acc(xs, a3);
+#pragma unroll
+  for (int c = 0; c < 3; c++) xs[c] = fma(hc4, v[c], fma(h2, fma(CKN::A42, a2[c], kmul(k, CKN::A41, a1[c])), x[c]));
+  acc(xs, a4);
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+    xs[c] = fma(h, v[c], fma(h2, fma(CKN::A53, a3[c], fma(CKN::A52, a2[c], kmul(k, CKN::A51, a1[c]))), x[c]));
+  acc(xs, a5);
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+    xs[c] = fma(hc6, v[c],
+                fma(h2, fma(CKN::A64, a4[c], fma(CKN::A63, a3[c], fma(CKN::A62, a2[c], kmul(k, CKN::A61, a1[c])))),
+                    x[c]));
+  acc(xs, a6);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    x5[c] = fma(h, v[c],
+                fma(h2, fma(CKN::B5, a5[c], fma(CKN::B4, a4[c], fma(CKN::B3, a3[c], kmul(k, CKN::B1, a1[c])))), x[c]));
+    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], kmul(k, CK::B1, a1[c])))), v[c]);
+    if (E) {
+      ex[c] = kmul(k, h2, fma(CKN::E5, a5[c], fma(CKN::E4, a4[c], fma(CKN::E3, a3[c], kmul(k, CKN::E1, a1[c])))));
+      ev[c] = kmul(k, h, fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], kmul(k, CK::E1, a1[c]))))));
+    }
+  }
+}
+
 template <int N, bool E>
 __device__ __forceinline__ void rkck_stages(const F64k &k, const double (&x)[3], const double (&v)[3], const double (&a1)[3],
                                             double m, int b, int base, double h, double (&x5)[3], double (&v5)[3],
                                             double (&ex)[3], double (&ev)[3]) {
-  constexpr int RT = ARing<N>::RTA;
-  double d2[RT];
-  double v2[3], v3[3], v4[3], v5s[3], v6[3];
-  double a2[3], a3[3], a4[3], a5[3], a6[3];
-  double xs[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, kmul(k, CK::A21, v[c]), x[c]);
-    v2[c] = fma(h, kmul(k, CK::A21, a1[c]), v[c]);
-  }
-  ring_acc<N, 0>(k, xs, m, b, base, a2, d2);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A32, v2[c], kmul(k, CK::A31, v[c])), x[c]);
-    v3[c] = fma(h, fma(CK::A32, a2[c], kmul(k, CK::A31, a1[c])), v[c]);
-  }
-  ring_acc<N, 0>(k, xs, m, b, base, a3, d2);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], kmul(k, CK::A41, v[c]))), x[c]);
-    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], kmul(k, CK::A41, a1[c]))), v[c]);
-  }
-  ring_acc<N, 0>(k, xs, m, b, base, a4, d2);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], kmul(k, CK::A51, v[c])))), x[c]);
-    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], kmul(k, CK::A51, a1[c])))), v[c]);
-  }
-  ring_acc<N, 0>(k, xs, m, b, base, a5, d2);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], kmul(k, CK::A61, v[c]))))),
-                x[c]);
-    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], kmul(k, CK::A61, a1[c]))))),
-                v[c]);
-  }
-  ring_acc<N, 0>(k, xs, m, b, base, a6, d2);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], kmul(k, CK::B1, v[c])))), x[c]);
-    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], kmul(k, CK::B1, a1[c])))), v[c]);
-    if (E) {
-      ex[c] = kmul(k, h, fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], kmul(k, CK::E1, v[c]))))));
-      ev[c] = kmul(k, h, fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], kmul(k, CK::E1, a1[c]))))));
-    }
-  }
+  double d2[ARing<N>::RTA];
+  rkck_step<E>(k, x, v, a1, h, [&](const double (&xs)[3], double (&a)[3]) { ring_acc<N, 0>(k, xs, m, b, base, a, d2); },
+               x5, v5, ex, ev);
 }
 
 // Body per lane: G = 32/N systems per warp, lane b of a group holds body b.  Work is

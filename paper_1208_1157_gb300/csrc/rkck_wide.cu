@@ -7,56 +7,15 @@
 
 namespace swarm {
 
-// one step of length h from (x, v) with first-stage acceleration a1 (see rkck_stages)
+// one step of length h from (x, v) with first-stage acceleration a1 (see rkck_step)
 template <bool E>
 __device__ __forceinline__ void wide_rkck_stages(const F64k &k, const double (&x)[3], const double (&v)[3], const double (&a1)[3],
                                                  double m, int b, const WideRing &R, double h, double (&x5)[3],
                                                  double (&v5)[3], double (&ex)[3], double (&ev)[3], double *d2s,
                                                  int lane) {
-  double v2[3], v3[3], v4[3], v5s[3], v6[3];
-  double a2[3], a3[3], a4[3], a5[3], a6[3];
-  double xs[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, kmul(k, CK::A21, v[c]), x[c]);
-    v2[c] = fma(h, kmul(k, CK::A21, a1[c]), v[c]);
-  }
-  wring_acc(k, xs, m, b, R, a2, d2s, lane);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A32, v2[c], kmul(k, CK::A31, v[c])), x[c]);
-    v3[c] = fma(h, fma(CK::A32, a2[c], kmul(k, CK::A31, a1[c])), v[c]);
-  }
-  wring_acc(k, xs, m, b, R, a3, d2s, lane);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A43, v3[c], fma(CK::A42, v2[c], kmul(k, CK::A41, v[c]))), x[c]);
-    v4[c] = fma(h, fma(CK::A43, a3[c], fma(CK::A42, a2[c], kmul(k, CK::A41, a1[c]))), v[c]);
-  }
-  wring_acc(k, xs, m, b, R, a4, d2s, lane);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A54, v4[c], fma(CK::A53, v3[c], fma(CK::A52, v2[c], kmul(k, CK::A51, v[c])))), x[c]);
-    v5s[c] = fma(h, fma(CK::A54, a4[c], fma(CK::A53, a3[c], fma(CK::A52, a2[c], kmul(k, CK::A51, a1[c])))), v[c]);
-  }
-  wring_acc(k, xs, m, b, R, a5, d2s, lane);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    xs[c] = fma(h, fma(CK::A65, v5s[c], fma(CK::A64, v4[c], fma(CK::A63, v3[c], fma(CK::A62, v2[c], kmul(k, CK::A61, v[c]))))),
-                x[c]);
-    v6[c] = fma(h, fma(CK::A65, a5[c], fma(CK::A64, a4[c], fma(CK::A63, a3[c], fma(CK::A62, a2[c], kmul(k, CK::A61, a1[c]))))),
-                v[c]);
-  }
-  wring_acc(k, xs, m, b, R, a6, d2s, lane);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    x5[c] = fma(h, fma(CK::B6, v6[c], fma(CK::B4, v4[c], fma(CK::B3, v3[c], kmul(k, CK::B1, v[c])))), x[c]);
-    v5[c] = fma(h, fma(CK::B6, a6[c], fma(CK::B4, a4[c], fma(CK::B3, a3[c], kmul(k, CK::B1, a1[c])))), v[c]);
-    if (E) {
-      ex[c] = kmul(k, h, fma(CK::E6, v6[c], fma(CK::E5, v5s[c], fma(CK::E4, v4[c], fma(CK::E3, v3[c], kmul(k, CK::E1, v[c]))))));
-      ev[c] = kmul(k, h, fma(CK::E6, a6[c], fma(CK::E5, a5[c], fma(CK::E4, a4[c], fma(CK::E3, a3[c], kmul(k, CK::E1, a1[c]))))));
-    }
-  }
+  rkck_step<E>(k, x, v, a1, h,
+               [&](const double (&xs)[3], double (&a)[3]) { wring_acc(k, xs, m, b, R, a, d2s, lane); }, x5, v5, ex,
+               ev);
 }
 
 // One system (index s) integrated for the whole call by the warp.
