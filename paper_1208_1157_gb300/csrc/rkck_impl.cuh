@@ -333,12 +333,321 @@ __device__ __forceinline__ void bpl_rkck_stream(const BinView &B, const StepPara
   }
 }
 
+// ---------------------------------------------------------------- system per lane
+// Accelerations (Eq. 1) of bodies k = 1..N-1 relative to body 0 from X_k = x_k - x_0:
+//   A_k = -m_0 s_k X_k - a_0 + sum_{i >= 1, i != k} m_i s_ik (X_i - X_k),
+//   a_0 = sum_{j >= 1} m_j s_j X_j  (stored in A[0]),  s = 1/r^3;
+// monitor distances q2[k] = |X_k|^2, d2[i][k] = |X_k - X_i|^2.
+template <int N>
+__device__ __forceinline__ void spl_acc_rel(const F64k &kk, const double (&X)[N][3], const double (&m)[N],
+                                            double (&A)[N][3], double (&q2)[N], double (&d2)[N][N]) {
+  double m0s[N];
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    double r2 = kmul(kk, X[k][0], X[k][0]);
+    r2 = fma(X[k][1], X[k][1], r2);
+    r2 = fma(X[k][2], X[k][2], r2);
+    const double rho = rsqrt(r2);
+    const double s3 = kmul(kk, kmul(kk, rho, rho), rho);
+    const double ms = kmul(kk, m[k], s3);
+    m0s[k] = kmul(kk, m[0], s3);
+    q2[k] = r2;
+#pragma unroll
+    for (int c = 0; c < 3; c++) A[0][c] = k == 1 ? kmul(kk, ms, X[k][c]) : fma(ms, X[k][c], A[0][c]);
+  }
+#pragma unroll
+  for (int k = 1; k < N; k++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) A[k][c] = fma(-m0s[k], X[k][c], -A[0][c]);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+      double dx[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) dx[c] = ksub(kk, X[k][c], X[i][c]);
+      double r2 = kmul(kk, dx[0], dx[0]);
+      r2 = fma(dx[1], dx[1], r2);
+      r2 = fma(dx[2], dx[2], r2);
+      const double rho = rsqrt(r2);
+      const double s3 = kmul(kk, kmul(kk, rho, rho), rho);
+      const double sk = kmul(kk, m[k], s3), si = kmul(kk, m[i], s3);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        A[i][c] = fma(sk, dx[c], A[i][c]);
+        A[k][c] = fma(-si, dx[c], A[k][c]);
+      }
+      d2[i][k] = r2;
+    }
+}
+
+// One Cash-Karp step (Nystrom form, see rkck_step) of every relative body of a lane's
+// system; with E also the error vectors, body 0's included (index 0: its velocity error
+// from its stage accelerations a_0, its position error -sum_k m_k ex_k / M from the
+// barycentre's fixed velocity, since sum_s (b5 - b4)_s = 0).  The monitor distances of
+// the last stage are discarded; the caller evaluates the accepted state.
+template <int N, bool E>
+__device__ __forceinline__ void spl_rkck_step(const F64k &k, const double (&x)[N][3], const double (&v)[N][3],
+                                              const double (&a1)[N][3], const double (&m)[N], double Minv,
+                                              double h, double (&x5)[N][3], double (&v5)[N][3],
+                                              double (&ex)[N][3], double (&ev)[N][3]) {
+  double a2[N][3], a3[N][3], a4[N][3], a5[N][3], a6[N][3], xs[N][3], q2[N], d2[N][N];
+  const double h2 = kmul(k, h, h);
+  const double hc2 = kmul(k, CKN::C2, h), hc3 = kmul(k, CKN::C3, h), hc4 = kmul(k, CKN::C4, h),
+               hc6 = kmul(k, CKN::C6, h);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) xs[i][c] = fma(hc2, v[i][c], x[i][c]);
+  spl_acc_rel<N>(k, xs, m, a2, q2, d2);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) xs[i][c] = fma(hc3, v[i][c], fma(h2, kmul(k, CKN::A31, a1[i][c]), x[i][c]));
+  spl_acc_rel<N>(k, xs, m, a3, q2, d2);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      xs[i][c] = fma(hc4, v[i][c], fma(h2, fma(CKN::A42, a2[i][c], kmul(k, CKN::A41, a1[i][c])), x[i][c]));
+  spl_acc_rel<N>(k, xs, m, a4, q2, d2);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      xs[i][c] = fma(h, v[i][c],
+                     fma(h2, fma(CKN::A53, a3[i][c], fma(CKN::A52, a2[i][c], kmul(k, CKN::A51, a1[i][c]))), x[i][c]));
+  spl_acc_rel<N>(k, xs, m, a5, q2, d2);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      xs[i][c] = fma(hc6, v[i][c],
+                     fma(h2,
+                         fma(CKN::A64, a4[i][c],
+                             fma(CKN::A63, a3[i][c], fma(CKN::A62, a2[i][c], kmul(k, CKN::A61, a1[i][c])))),
+                         x[i][c]));
+  spl_acc_rel<N>(k, xs, m, a6, q2, d2);
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      x5[i][c] = fma(h, v[i][c],
+                     fma(h2, fma(CKN::B5, a5[i][c], fma(CKN::B4, a4[i][c], fma(CKN::B3, a3[i][c], kmul(k, CKN::B1, a1[i][c])))),
+                         x[i][c]));
+      v5[i][c] = fma(h, fma(CK::B6, a6[i][c], fma(CK::B4, a4[i][c], fma(CK::B3, a3[i][c], kmul(k, CK::B1, a1[i][c])))),
+                     v[i][c]);
+    }
+  if (E) {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        if (i > 0)
+          ex[i][c] = kmul(k, h2, fma(CKN::E5, a5[i][c], fma(CKN::E4, a4[i][c], fma(CKN::E3, a3[i][c], kmul(k, CKN::E1, a1[i][c])))));
+        ev[i][c] = kmul(k, h, fma(CK::E6, a6[i][c], fma(CK::E5, a5[i][c], fma(CK::E4, a4[i][c], fma(CK::E3, a3[i][c], kmul(k, CK::E1, a1[i][c]))))));
+      }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double sx = 0.0;
+#pragma unroll
+      for (int i = 1; i < N; i++) sx = fma(m[i], ex[i][c], sx);
+      ex[0][c] = kmul(k, -sx, Minv);
+    }
+  }
+}
+
+// System per lane (n <= 3), coordinates relative to body 0 plus the barycentre (the
+// same method in exact arithmetic: every stage is linear in the state and the stage
+// accelerations, and A_k = a_k - a_0), work handed out per lane: a lane whose system
+// reached its end time or stopped takes the bin's next one.  Step rules, error norm
+// (in inertial coordinates, rebuilt from the relative ones) and step control are those
+// of bpl_rkck_stream.
+template <int N, bool ADAPT>
+__device__ __forceinline__ void spl_rkck_stream(const BinView &B, const StepParams &P) {
+  constexpr unsigned long long NP = (unsigned long long)N * (N - 1) / 2;
+  const unsigned FULL = 0xffffffffu;
+  const int SP = B.S_pad;
+  const double dir = P.dt > 0 ? 1.0 : -1.0;
+  const int nmax = ADAPT ? (P.max_steps > 0 ? P.max_steps : kRkckTrialCap) : 0;
+  const double inv_eps2 = 1.0 / (P.rk_eps * P.rk_eps);
+  double x[N][3], v[N][3], m[N], a1[N][3], kc[N][N], q2[N], d2[N][N];
+  double Minv = 1.0, Xc[3] = {0.0, 0.0, 0.0}, Vc[3] = {0.0, 0.0, 0.0};
+  LaunchPlan plan;
+  plan.N = 0;
+  plan.full = 1;
+  plan.exact = 1;
+  plan.h_last = P.dt;
+  plan.t_end = P.t_end;
+  double t = 0.0, t0 = 0.0, te = 0.0, h = fabs(P.dt);
+  int s = 0, steps = 0, trials = 0;
+  bool has = false, exhausted = false;
+  for (;;) {
+    if (!has && !exhausted) {
+      s = stream_system(B, atomicAdd(P.work_next, 1));
+      if (s < 0) {
+        exhausted = true;
+      } else {
+        const bool runnable = B.status[s] <= SWARM_SYS_DONE;
+        t0 = B.t[s];
+        bool go;
+        if (!ADAPT) {
+          plan = launch_plan(B, P, s, t0, runnable);
+          te = plan.t_end;
+          go = runnable && plan.N > 0;
+        } else {
+          te = B.t_end ? B.t_end[s] : (P.t_end_dev ? *P.t_end_dev : P.t_end);
+          go = runnable && ((te - t0) * dir > 1e-12 * fmax(1.0, fabs(te)));
+        }
+        if (runnable && !go) B.status[s] = SWARM_SYS_DONE;
+        if (go) {
+#pragma unroll
+          for (int i = 0; i < N; i++) {
+            m[i] = B.m[(size_t)i * SP + s];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              x[i][c] = B.x[(size_t)(c * N + i) * SP + s];
+              v[i][c] = B.v[(size_t)(c * N + i) * SP + s];
+            }
+          }
+#pragma unroll
+          for (int i = 1; i < N; i++)
+#pragma unroll
+            for (int k = i + 1; k < N; k++) kc[i][k] = hill_kc(P.ce_factor, m[i], m[k], m[0]);
+          spl_to_rel<N>(m, x, v, Minv, Xc, Vc);
+          spl_acc_rel<N>(P.fk, x, m, a1, q2, d2);
+          t = t0;
+          steps = 0;
+          trials = 0;
+          h = fabs(P.dt);
+          has = true;
+        }
+      }
+    }
+    if (!__any_sync(FULL, has || !exhausted)) break;
+    if (!has) continue;
+
+    // ---- one step (or trial)
+    double hs;
+    bool last;
+    if (!ADAPT) {
+      last = steps + 1 == plan.N;
+      hs = (last && !plan.exact) ? plan.h_last : P.dt;
+    } else {
+      const double rem = kmul(P.fk, ksub(P.fk, te, t), dir);
+      last = h >= rem;
+      hs = kmul(P.fk, last ? rem : h, dir);
+    }
+    double x5[N][3], v5[N][3], ex[N][3], ev[N][3];
+    spl_rkck_step<N, ADAPT>(P.fk, x, v, a1, m, Minv, hs, x5, v5, ex, ev);
+    bool accept = true;
+    double err = 0.0;  // adaptive: the squared scaled error of the trial
+    bool bad = false;
+    if (ADAPT) {
+      double xi[N][3], vi[N][3];
+      spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xi, vi);
+      double X2 = 0.0, V2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        X2 = fmax(X2, fma(xi[i][2], xi[i][2], fma(xi[i][1], xi[i][1], kmul(P.fk, xi[i][0], xi[i][0]))));
+        V2 = fmax(V2, fma(vi[i][2], vi[i][2], fma(vi[i][1], vi[i][1], kmul(P.fk, vi[i][0], vi[i][0]))));
+      }
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        double e[3], f[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          e[c] = i == 0 ? ex[0][c] : kadd(P.fk, ex[i][c], ex[0][c]);
+          f[c] = i == 0 ? ev[0][c] : kadd(P.fk, ev[i][c], ev[0][c]);
+        }
+        const double px = fma(e[2], e[2], fma(e[1], e[1], kmul(P.fk, e[0], e[0])));
+        const double pv = fma(f[2], f[2], fma(f[1], f[1], kmul(P.fk, f[0], f[0])));
+        err = fmax(err, rk_err2(px, pv, X2, V2, inv_eps2));
+      }
+      bad = nonfinite(err);
+      accept = !bad && err <= 1.0;
+      trials++;
+    }
+    if (accept) {
+#pragma unroll
+      for (int i = 1; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          x[i][c] = x5[i][c];
+          v[i][c] = v5[i][c];
+        }
+#pragma unroll
+      for (int c = 0; c < 3; c++) Xc[c] = fma(hs, Vc[c], Xc[c]);
+      spl_acc_rel<N>(P.fk, x, m, a1, q2, d2);
+      steps++;
+      if (ADAPT) t = last ? te : kadd(P.fk, t, hs);
+    }
+    int code = 0;
+    if (accept) {
+      bool nf = false, ej = false, ce = false;
+#pragma unroll
+      for (int i = 1; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
+#pragma unroll
+      for (int i = 1; i < N; i++) ej |= (P.eject2 > 0.0) && (q2[i] > P.eject2);
+#pragma unroll
+      for (int i = 1; i < N; i++)
+#pragma unroll
+        for (int k2 = i + 1; k2 < N; k2++)
+          if (kc[i][k2] > 0.0 && close_encounter(P.fk, d2[i][k2], kc[i][k2], q2[i], q2[k2])) ce = true;
+      code = nf ? SWARM_SYS_NONFINITE : ej ? SWARM_SYS_EJECTED : ce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+    }
+    if (bad) code = SWARM_SYS_NONFINITE;
+    const bool reached = accept && last && !code;
+    if (!ADAPT && accept && (code || reached || (P.log_interval > 0 && (steps % P.log_interval) == 0)))
+      t = step_time(plan, steps, t0, P.dt);  // fixed steps: time formed when it is used
+    if (P.log_interval > 0 && accept && !code && (steps % P.log_interval) == 0) {
+      double xo[N][3], vo[N][3], e4[4];
+      spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
+      spl_energy<N>(xo, vo, m, e4);
+      write_log(P, B.gidx[s], t, e4);
+    }
+    if (ADAPT && !code && !reached) {
+      double f;  // 0.9 err^(-1/5), from the squared error
+      if (err <= 1e-30) f = 5.0;
+      else if (err >= 1e30) f = 0.2;
+      else f = 0.9 * inv_tenth_root(err);
+      h = fabs(hs) * (accept ? fmin(5.0, fmax(0.2, f)) : fmax(0.2, f));
+      if (!(h > 0.0) || nonfinite(h) || t + dir * h == t) code = SWARM_SYS_NONFINITE;  // step-size underflow
+    }
+    const bool capped = ADAPT && trials >= nmax;
+    if (code != 0 || reached || capped) {
+      double xo[N][3], vo[N][3];
+      spl_from_rel<N>(m, x, v, Minv, Xc, Vc, xo, vo);
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          B.x[(size_t)(c * N + i) * SP + s] = xo[i][c];
+          B.v[(size_t)(c * N + i) * SP + s] = vo[i][c];
+        }
+      B.t[s] = t;
+      if (code) B.status[s] = code;
+      else if (ADAPT) B.status[s] = reached ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+      else B.status[s] = plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE;
+      if (P.counters) {
+        const unsigned long long tr = ADAPT ? (unsigned long long)trials : (unsigned long long)steps;
+        if (steps > 0) atomicAdd(&P.counters[0], (unsigned long long)steps);
+        atomicAdd(&P.counters[1], NP * (1ull + 6ull * tr));
+      }
+      has = false;
+    }
+  }
+}
+
 // Persistent kernel for one bin: every warp streams systems through its groups until the
 // bin's counter runs out (work unit = system).
 template <int N, bool ADAPT>
 __global__ void __launch_bounds__(128, 2) rkck_uniform_kernel(BinView B, int nunits, StepParams P) {
   (void)nunits;
-  bpl_rkck_stream<N, ADAPT>(B, P);
+  if (N <= 3) spl_rkck_stream<N, ADAPT>(B, P);  // system per lane
+  else bpl_rkck_stream<N, ADAPT>(B, P);
 }
 
 template <int N, bool ADAPT>
