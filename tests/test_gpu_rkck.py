@@ -81,7 +81,9 @@ def test_rkck_chunked_graph_launches_equal_one_launch():
     chunked = run_gpu(ens, 1000 * DT, RKCK, DT, steps_per_launch=100)
     assert chunked["stats"]["kernel_launches"] == 10
     ex, ev = per_system_errors(ens, chunked, one)
-    assert ex.max() == 0.0 and ev.max() == 0.0
+    # every launch boundary rounds the state once through inertial coordinates (the
+    # 3-body kernel steps coordinates relative to body 0): agreement to round-off
+    assert ex.max() <= 1e-14 and ev.max() <= 1e-14
 
 
 def test_rkck_tolerance_is_checked():
