@@ -163,10 +163,13 @@ struct ChiState {
 // first step of a call: Vallado's guess).  Executed by every lane of the warp; lanes with
 // `on` false do not change their state.  Returns false on non-convergence in 50
 // iterations.
+// RQ: rq holds 1/|r| of the current r on entry (computed by the same expression); on exit
+// the lanes that drifted hold 1/|r| of the new r there.
+template <bool RQ>
 static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const KepConst &K, double (&r)[3], double (&v)[3],
-                                                 double h, ChiState &cs, int &iters) {
+                                                 double h, ChiState &cs, int &iters, double &rq) {
   const double r2 = fma(r[2], r[2], fma(r[1], r[1], kmul(k, r[0], r[0])));
-  const double rinv0 = rsqrt(r2);
+  const double rinv0 = RQ ? rq : rsqrt(r2);
   const double r0 = kmul(k, r2, rinv0);
   const double sig0 = fma(r[2], v[2], fma(r[1], v[1], kmul(k, r[0], v[0])));
   const double v2 = fma(v[2], v[2], fma(v[1], v[1], kmul(k, v[0], v[0])));
@@ -240,6 +243,7 @@ static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const Ke
   cs.prev = cs.chi;
   cs.chi = x;
   cs.n = cs.n < 2 ? cs.n + 1 : 2;
+  rq = rinv;
   return true;
 }
 
@@ -318,10 +322,11 @@ __device__ __forceinline__ void jacobi_helio(const F64k &k, const double (&q)[3]
 
 // Interaction acceleration.  DH: planet-planet terms (Sec. 2.2.3).  Jacobi: Jacobi
 // components of all pair accelerations plus mu_b r'_b/|r'_b|^3.
-template <int N, bool JAC>
+// RQ (Jacobi): rq holds 1/|q| on entry; otherwise it is computed and stored there.
+template <int N, bool JAC, bool RQ = false>
 __device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], double m, double w, double eta_prev_inv, double mu,
                                         int b, int base, double (&acc)[3], double (&Q)[3],
-                                        double (&d2)[ARing<(JAC ? N : N - 1)>::RTA]) {
+                                        double (&d2)[ARing<(JAC ? N : N - 1)>::RTA], double &rq) {
   if constexpr (!JAC) {
     ring_acc<N - 1, 1>(fk, q, m, b == 0 ? 0 : b - 1, base, acc, d2);
 #pragma unroll
@@ -333,8 +338,13 @@ __device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], do
     jacobi_helio<N>(fk, q, w, b, Q);
     double a[3];
     ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
-    const double r2 = fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0])));
-    const double rho = rsqrt(r2);
+    double rho;
+    if (RQ) {
+      rho = rq;
+    } else {
+      rho = rsqrt(fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0]))));
+      rq = rho;
+    }
     const double k = kmul(fk, kmul(fk, kmul(fk, mu, rho), rho), rho);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -416,7 +426,8 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
   double acc[3], Q[3], d2[RTA];
 #pragma unroll
   for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-  mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+  double rq = 1.0;  // Jacobi: 1/|q| of the current q (planets)
+  mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2, rq);
 
   bool alive = runnable;
   int steps_done = 0;
@@ -446,10 +457,10 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     // Keplerian drift of every planet
     int its = 0;
-    bool ok = kepler_drift(P.fk, active && b != 0, K, q, u, h, cs, its);
+    bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, cs, its, rq);
     kep_iters += its;
     // accelerations at the new positions, reused by the next step's first kick
-    mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+    mvs_acc<N, JAC, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2, rq);
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     if (!JAC) {
@@ -599,6 +610,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
   double t0 = 0.0;
   int kg = 0;
   double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
+  double rq = 1.0;  // Jacobi: 1/|q| of the current q (planets)
   ChiState cs;
   unsigned long long kep_iters = 0;
 #pragma unroll
@@ -651,8 +663,10 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       double an[3], Qn[3], d2n[RTA];
 #pragma unroll
       for (int r = 0; r < RTA; r++) d2n[r] = 0.0;
-      mvs_acc<N, JAC>(P.fk, qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n);
+      double rqn = 1.0;
+      mvs_acc<N, JAC>(P.fk, qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n, rqn);
       if (take) {
+        rq = rqn;
         s = ss;
         const double tn = B.t[s];
         const bool runnable = B.status[s] <= SWARM_SYS_DONE;
@@ -692,12 +706,12 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(P.fk, active && b != 0, K, q, u, h, cs, its);
+    const bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, cs, its, rq);
     kep_iters += its;
     double Q[3], d2[RTA];
 #pragma unroll
     for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-    mvs_acc<N, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2);
+    mvs_acc<N, JAC, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2, rq);
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     if (!JAC) {

@@ -222,7 +222,8 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift(P.fk, real && b != 0, K, q, u, h, cs, its);
+    double rqw = 1.0;
+    const bool ok = kepler_drift<false>(P.fk, real && b != 0, K, q, u, h, cs, its, rqw);
     kep_iters += its;
     wide_mvs_acc<JAC>(P.fk, q, W, b, n, real, lane, acc, Q, d2s);
 #pragma unroll
