@@ -122,7 +122,7 @@ def two_body_error(e, N, form=O.CORR_KOKUBO, periods=1.0):
 
 @pytest.mark.parametrize("e", [0.0, 0.5])
 def test_hermite_two_body_orbit_closes_after_one_period(e):
-    # the benchmark spec pin: orbit closure to 1e-9 relative after one period with dt = T/4000
+    # orbit closure to 1e-9 relative after one period with dt = T/4000
     assert two_body_error(e, 4000) <= 1e-9
 
 
