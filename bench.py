@@ -308,8 +308,8 @@ def secondary(S, torch, stream):
     out["c2_persistent_system_per_lane_3cta_500"] = timed(c2, 500 * DT, S.HERMITE4, DT, mapping=S.MAP_SYSTEM_PER_LANE,
                                                           ctas=3)
     c3 = ics.ragged(65536, seed=3)
-    out["c3_ragged_hermite_per_bin_launches_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT)
-    out["c3_ragged_hermite_single_launch_100_steps"] = timed_per_bin(S, stream, c3, 100 * DT, DT, single=1)
+    out["c3_ragged_hermite_per_bin_launches_1e4_steps"] = timed_per_bin(S, stream, c3, 1e4 * DT, DT)
+    out["c3_ragged_hermite_single_launch_1e4_steps"] = timed_per_bin(S, stream, c3, 1e4 * DT, DT, single=1)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
     out["c4_mvs_jacobi_2000_steps_2cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=2)
