@@ -146,11 +146,12 @@ static __device__ __noinline__ double chi_guess(const KepConst &K, const double 
 
 // Universal-variable Kepler drift of (r, v) by h: Newton on
 //   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
-// Starting point of the next Kepler solve of a planet: its last two solutions, which
-// (steps of equal length) extrapolate linearly to within the orbit's second difference.
+// Starting point of the next Kepler solve of a planet: its last three solutions, which
+// (steps of equal length) extrapolate quadratically to within the orbit's third
+// difference (linearly from two, the last one alone after the first step).
 struct ChiState {
-  double chi = 0.0, prev = 0.0;
-  int n = 0;  // solutions held (0, 1, 2)
+  double chi = 0.0, prev = 0.0, prev2 = 0.0;
+  int n = 0;  // solutions held (0..3)
 };
 
 // Universal-variable Kepler drift of (r, v) by h: Newton on
@@ -177,7 +178,7 @@ static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const Ke
   const double s0 = kmul(k, sig0, K.smuinv);
   const double beta = fma(-alpha, r0, 1.0);
   const double target = kmul(k, K.smu, h);
-  double x = cs.n >= 2 ? 2.0 * cs.chi - cs.prev : cs.chi;
+  double x = cs.n >= 3 ? fma(3.0, ksub(k, cs.chi, cs.prev), cs.prev2) : cs.n == 2 ? 2.0 * cs.chi - cs.prev : cs.chi;
   if (on && cs.n == 0) x = chi_guess(K, r, v, r0, sig0, alpha, h);
   bool done = !on;
   int it = 0;
@@ -240,9 +241,10 @@ static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const Ke
     v[c] = fma(fd, r[c], kmul(k, gd, v[c]));
     r[c] = rn[c];
   }
+  cs.prev2 = cs.prev;
   cs.prev = cs.chi;
   cs.chi = x;
-  cs.n = cs.n < 2 ? cs.n + 1 : 2;
+  cs.n = cs.n < 3 ? cs.n + 1 : 3;
   rq = rinv;
   return true;
 }
