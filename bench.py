@@ -324,6 +324,12 @@ def secondary(S, torch, stream):
     out["c2_rkck_fixed_1cta_500"] = timed(c2, 500 * DT, S.RKCK, DT, ctas=1)
     out["c2_rkck_adaptive_eps_1e-12_one_period"] = timed(c2, TWO_PI, S.RKCK_ADAPTIVE, 0.05)
     out["c3_ragged_rkck_100_steps"] = timed(c3, 100 * DT, S.RKCK, DT)
+    # the ragged batch against the plain one-launch-per-step kernel on the same systems
+    # (the plain kernel has n <= 8): 65536 systems, n = 3..8, 500 steps
+    c3s = ics.ragged(65536, seed=3, n_max=8)
+    out["c3_ragged_n3_8_plain_one_launch_per_step_500"] = timed(c3s, 500 * DT, S.HERMITE4, DT,
+                                                               mapping=S.MAP_PLAIN_PER_STEP)
+    out["c3_ragged_n3_8_persistent_500"] = timed(c3s, 500 * DT, S.HERMITE4, DT)
     c6 = ics.ragged_wide(16384, seed=6)
     out["wide_16_to_32_bodies_hermite_20_steps"] = timed(c6, 20 * DT, S.HERMITE4, DT)
     out["wide_16_to_32_bodies_mvs_jacobi_100_steps"] = timed(c6, 100 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
