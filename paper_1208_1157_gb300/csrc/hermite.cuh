@@ -437,6 +437,138 @@ __device__ __forceinline__ void spl_accjerk_rel(const F64k &kk, const double (&X
     }
 }
 
+// 1/|d| and its square for each pair of a system per lane (index [0][k]: body 0 with body
+// k; [i][k], 1 <= i < k: bodies i and k), kept from one evaluation of a step to the next.
+template <int N>
+struct RhoCache {
+  double r[N][N], r2[N][N];
+};
+
+// rsqrt out of line: the rare branch of spl_accjerk_rel_cached
+static __device__ __noinline__ double rsqrt_call(double x) { return rsqrt(x); }
+
+// spl_accjerk_rel for the evaluations of a step after its first: the positions have moved
+// by the corrector only, so each 1/|d| follows from the previous evaluation's value rho_o
+// by the series of (1 + delta)^(-1/2), delta = |d|^2 rho_o^2 - 1:
+//   rho = rho_o (1 - delta/2 + 3 delta^2/8),  error 5|delta|^3/16,
+// taken when |delta| < 1e-6 for every pair of the lane (error below 3.2e-19; on the
+// 131072 x 3 ensemble delta ~ 1e-10), else rsqrt.  FIRST: the step's first evaluation
+// (rsqrt, filling the cache).  Same outputs as spl_accjerk_rel.
+template <int N, bool FIRST>
+__device__ __forceinline__ void spl_accjerk_rel_cached(const F64k &kk, const double (&X)[N][3],
+                                                       const double (&V)[N][3], const double (&m)[N],
+                                                       double (&A)[N][3], double (&J)[N][3], double (&q2)[N],
+                                                       double (&d2)[N][N], RhoCache<N> &rc) {
+  // geometry of every pair
+  double rv[N][N], dx[N][N][3], dv[N][N][3], rho[N][N];
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    double r2 = kmul(kk, X[k][0], X[k][0]);
+    r2 = fma(X[k][1], X[k][1], r2);
+    r2 = fma(X[k][2], X[k][2], r2);
+    double t = kmul(kk, X[k][0], V[k][0]);
+    t = fma(X[k][1], V[k][1], t);
+    rv[0][k] = fma(X[k][2], V[k][2], t);
+    q2[k] = r2;
+  }
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        dx[i][k][c] = ksub(kk, X[k][c], X[i][c]);
+        dv[i][k][c] = ksub(kk, V[k][c], V[i][c]);
+      }
+      double r2 = kmul(kk, dx[i][k][0], dx[i][k][0]);
+      r2 = fma(dx[i][k][1], dx[i][k][1], r2);
+      r2 = fma(dx[i][k][2], dx[i][k][2], r2);
+      double t = kmul(kk, dx[i][k][0], dv[i][k][0]);
+      t = fma(dx[i][k][1], dv[i][k][1], t);
+      rv[i][k] = fma(dx[i][k][2], dv[i][k][2], t);
+      d2[i][k] = r2;
+    }
+  auto dist2 = [&](int i, int k) -> double { return i == 0 ? q2[k] : d2[i][k]; };
+  if (FIRST) {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int k = (i == 0 ? 1 : i + 1); k < N; k++) rho[i][k] = rsqrt(dist2(i, k));
+  } else {
+    double del[N][N];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int k = (i == 0 ? 1 : i + 1); k < N; k++) {
+        del[i][k] = fma(dist2(i, k), rc.r2[i][k], -1.0);
+        ok &= fabs(del[i][k]) < 1e-6;
+      }
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int k = (i == 0 ? 1 : i + 1); k < N; k++)
+          rho[i][k] = fma(kmul(kk, rc.r[i][k], del[i][k]), fma(0.375, del[i][k], -0.5), rc.r[i][k]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int k = (i == 0 ? 1 : i + 1); k < N; k++) rho[i][k] = rsqrt_call(dist2(i, k));
+    }
+  }
+  // body 0's pairs: A_k = -m_0 s_k X_k - a_0, a_0 = sum_j m_j s_j X_j (likewise J)
+  double w0[N][3], m0s[N], IA[3], IJ[3];
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    const double rho2 = kmul(kk, rho[0][k], rho[0][k]);
+    rc.r[0][k] = rho[0][k];
+    rc.r2[0][k] = rho2;
+    const double s3 = kmul(kk, rho2, rho[0][k]);
+    const double cc = kmul(kk, -3.0, kmul(kk, rv[0][k], rho2));
+    const double ms = kmul(kk, m[k], s3);
+    m0s[k] = kmul(kk, m[0], s3);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      w0[k][c] = fma(cc, X[k][c], V[k][c]);
+      IA[c] = k == 1 ? kmul(kk, ms, X[k][c]) : fma(ms, X[k][c], IA[c]);
+      IJ[c] = k == 1 ? kmul(kk, ms, w0[k][c]) : fma(ms, w0[k][c], IJ[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    A[0][c] = IA[c];
+    J[0][c] = IJ[c];
+  }
+#pragma unroll
+  for (int k = 1; k < N; k++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      A[k][c] = fma(-m0s[k], X[k][c], -IA[c]);
+      J[k][c] = fma(-m0s[k], w0[k][c], -IJ[c]);
+    }
+  // pairs of bodies i, k >= 1
+#pragma unroll
+  for (int i = 1; i < N; i++)
+#pragma unroll
+    for (int k = i + 1; k < N; k++) {
+      const double rho2 = kmul(kk, rho[i][k], rho[i][k]);
+      rc.r[i][k] = rho[i][k];
+      rc.r2[i][k] = rho2;
+      const double rho3 = kmul(kk, rho2, rho[i][k]);
+      const double cc = kmul(kk, -3.0, kmul(kk, rv[i][k], rho2));
+      const double sk = kmul(kk, m[k], rho3), si = kmul(kk, m[i], rho3);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const double w = fma(cc, dx[i][k][c], dv[i][k][c]);
+        A[i][c] = fma(sk, dx[i][k][c], A[i][c]);
+        J[i][c] = fma(sk, w, J[i][c]);
+        A[k][c] = fma(-si, dx[i][k][c], A[k][c]);
+        J[k][c] = fma(-si, w, J[k][c]);
+      }
+    }
+}
+
 template <int N>
 __device__ __forceinline__ void spl_energy(const double (&x)[N][3], const double (&v)[N][3], const double (&m)[N],
                                            double (&out)[4]) {

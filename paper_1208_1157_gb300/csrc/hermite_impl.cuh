@@ -221,6 +221,10 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 
   double a0[N][3], j0[N][3], q2[N], d2[N][N];
   spl_accjerk_rel<N>(P.fk, x, v, m, a0, j0, q2, d2);
+  // 1/|d| carried from evaluation to evaluation within a step (three bodies and fewer:
+  // the registers of four do not fit)
+  constexpr bool kCache = N <= 3;
+  RhoCache<N> rc;
   const HCoef cdt = hcoef(P.dt);
   const HCoef clast = hcoef(plan.h_last);
   int steps_done = 0;
@@ -254,7 +258,9 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
     }
     for (int ic = 0; ic < P.n_corr; ic++) {
       double ak[N][3], jk[N][3];
-      spl_accjerk_rel<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
+      if (!kCache) spl_accjerk_rel<N>(P.fk, xk, vk, m, ak, jk, q2, d2);
+      else if (ic == 0) spl_accjerk_rel_cached<N, true>(P.fk, xk, vk, m, ak, jk, q2, d2, rc);
+      else spl_accjerk_rel_cached<N, false>(P.fk, xk, vk, m, ak, jk, q2, d2, rc);
 #pragma unroll
       for (int i = 1; i < N; i++)
 #pragma unroll
@@ -271,7 +277,8 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
           for (int c = 0; c < 3; c++) xk[i][c] = fma(-C.h2_12, ak[i][c], fma(C.hh, vk[i][c], XB(i, c)));
       }
     }
-    spl_accjerk_rel<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
+    if (!kCache || P.n_corr == 0) spl_accjerk_rel<N>(P.fk, xk, vk, m, a0, j0, q2, d2);
+    else spl_accjerk_rel_cached<N, false>(P.fk, xk, vk, m, a0, j0, q2, d2, rc);
 #pragma unroll
     for (int i = 1; i < N; i++)
 #pragma unroll
