@@ -77,6 +77,12 @@ __device__ __forceinline__ bool nonfinite(double a) {
   return (__double2hiint(a) & 0x7ff00000) == 0x7ff00000;
 }
 
+// a < b for non-negative doubles (and NaN, which orders above +inf) on the bit patterns:
+// an integer compare instead of an FP64 one.
+__device__ __forceinline__ bool nonneg_lt(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
 // Per-system step plan of Algorithm 1 with a shortened last step: N = round(D) when
 // D = (t_end - t)/dt is within 1e-9 of an integer, else ceil(D).
 struct StepPlan {

@@ -596,7 +596,7 @@ __device__ __forceinline__ void spl_energy(const double (&x)[N][3], const double
 // (q_i + q_j)^2 <= 2 (q_i^2 + q_j^2) rules most pairs out without a square root.
 __device__ __forceinline__ bool close_encounter(const F64k &k, double d2, double kc, double q2i, double q2j) {
   double t = kadd(k, q2i, q2j);
-  if (d2 < kmul(k, kmul(k, 2.0, kc), t)) {
+  if (nonneg_lt(d2, kmul(k, kmul(k, 2.0, kc), t))) {  // squared distances: integer compare
     double s = sqrt(q2i) + sqrt(q2j);
     return d2 < kc * (s * s);
   }

@@ -295,7 +295,7 @@ __device__ __forceinline__ void spl_hermite_body(const BinView &B, const StepPar
 #pragma unroll
       for (int c = 0; c < 3; c++) nf |= nonfinite(x[i][c]) | nonfinite(v[i][c]);
 #pragma unroll
-    for (int i = 1; i < N; i++) ej |= ej_on && (q2[i] > P.eject2);
+    for (int i = 1; i < N; i++) ej |= ej_on && nonneg_lt(P.eject2, q2[i]);
 #pragma unroll
     for (int i = 1; i < N; i++)
 #pragma unroll
