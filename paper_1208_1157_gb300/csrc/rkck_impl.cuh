@@ -41,9 +41,9 @@ __device__ __forceinline__ double grp_max(double val, int b, int base) {
   return shfl(val, base);
 }
 
-// e^(-1/10) to FP64 accuracy (the step-control factor err^(-1/5) from the squared error
-// e = err^2): a single-precision estimate refined by one Newton step on y^-10 = e
-// (y <- y (11 - e y^10) / 10); e in [1e-30, 1e30].
+// e^(-1/10) (the step-control factor err^(-1/5) from the squared error e = err^2): a
+// single-precision estimate, relative error d ~ 1e-7, refined by one Newton step on
+// y^-10 = e (y <- y (11 - e y^10) / 10), which leaves 5.5 d^2 ~ 1e-12; e in [1e-30, 1e30].
 __device__ __forceinline__ double inv_tenth_root(double e) {
   const float yf = exp2f(-0.1f * log2f((float)e));
   const double y = (double)yf;

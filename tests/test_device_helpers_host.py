@@ -1,4 +1,5 @@
-"""The Stumpff functions of the Kepler drift (csrc/mvs_impl.cuh, `stumpff23`: power series
+"""Device helpers compiled from the kernel sources as host code (no GPU: gcc and the
+source text).  The Stumpff functions of the Kepler drift (csrc/mvs_impl.cuh, `stumpff23`: power series
 to |z| <= 0.25, argument quartering and the doubling relations beyond), compiled from the
 kernel source as host code and checked against the closed forms
     c2(z) = (1 - cos sqrt z) / z,  c3(z) = (sqrt z - sin sqrt z) / z^(3/2)
@@ -85,3 +86,31 @@ def test_universal_identity(stumpff_exe):
     c0 = 1 - zs * c2
     c1 = 1 - zs * c3
     assert np.max(np.abs(c0 * c0 + zs * c1 * c1 - 1.0) / np.maximum(1.0, c0 * c0)) <= 1e-12
+
+
+RK = os.path.join(os.path.dirname(SRC), "rkck_impl.cuh")
+
+
+def test_step_control_root_host():
+    # inv_tenth_root (the Runge-Kutta step control's err^(-1/5) from the squared error),
+    # compiled from the kernel source as host code: e^(-1/10) to ~1e-12 over [1e-30, 1e30]
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import tempfile
+    text = open(RK).read()
+    fn = re.search(r"__device__ __forceinline__ double inv_tenth_root\(double e\) \{.*?\n\}\n", text,
+                   re.S).group(0).replace("__device__ __forceinline__ ", "static ")
+    prog = ("#include <cmath>\n#include <cstdio>\nusing std::fma; using std::exp2f; using std::log2f;\n" + fn +
+            "int main() { double e; while (scanf(\"%lf\", &e) == 1) printf(\"%.17g\\n\", inv_tenth_root(e)); return 0; }\n")
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "r.cpp"), "w") as f:
+        f.write(prog)
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-o", os.path.join(d, "r"), os.path.join(d, "r.cpp")],
+                   check=True)
+    es = np.logspace(-30, 30, 601)
+    out = subprocess.run([os.path.join(d, "r")], input="\n".join(repr(float(e)) for e in es), capture_output=True,
+                         text=True, check=True).stdout.split()
+    mp.mp.dps = 30
+    err = max(abs(float((mp.mpf(y) - mp.power(mp.mpf(e), mp.mpf(-1) / 10)) / mp.power(mp.mpf(e), mp.mpf(-1) / 10)))
+              for y, e in zip(out, es))
+    assert err <= 5e-12, err
