@@ -1,9 +1,10 @@
 """Device helpers compiled from the kernel sources as host code (no GPU: gcc and the
-source text).  The Stumpff functions of the Kepler drift (csrc/mvs_impl.cuh, `stumpff23`: power series
-to |z| <= 0.25, argument quartering and the doubling relations beyond), compiled from the
-kernel source as host code and checked against the closed forms
+source text), checked in 30-50 digit arithmetic: the Stumpff functions of the Kepler drift
+(csrc/mvs_impl.cuh, `stumpff23`: power series to |z| <= 0.25, argument quartering and the
+doubling relations beyond) against the closed forms
     c2(z) = (1 - cos sqrt z) / z,  c3(z) = (sqrt z - sin sqrt z) / z^(3/2)
-(cosh / sinh for z < 0) in 50-digit arithmetic.  No GPU: gcc and the source text."""
+(cosh / sinh for z < 0), and the Runge-Kutta step control's e^(-1/10)
+(csrc/rkck_impl.cuh, `inv_tenth_root`)."""
 import os
 import re
 import shutil
