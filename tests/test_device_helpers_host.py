@@ -115,3 +115,126 @@ def test_step_control_root_host():
     err = max(abs(float((mp.mpf(y) - mp.power(mp.mpf(e), mp.mpf(-1) / 10)) / mp.power(mp.mpf(e), mp.mpf(-1) / 10)))
               for y, e in zip(out, es))
     assert err <= 5e-12, err
+
+
+COMMON = os.path.join(os.path.dirname(SRC), "common.cuh")
+
+KEPLER_MAIN = r"""
+int main() {
+  // per line: mu h steps rx ry rz vx vy vz; prints the state after every step and the
+  // Newton iterations of that step
+  double mu, h, r[3], v[3];
+  int steps;
+  const swarm::F64k k = {0.0, -1.0, 1.0};
+  while (scanf("%lf %lf %d %lf %lf %lf %lf %lf %lf", &mu, &h, &steps, &r[0], &r[1], &r[2], &v[0], &v[1], &v[2]) == 9) {
+    const swarm::KepConst K = swarm::kep_const(mu);
+    swarm::ChiState cs;
+    double rq = 1.0;
+    for (int s = 0; s < steps; s++) {
+      int it = 0;
+      const bool ok = swarm::kepler_drift<false>(k, true, K, r, v, h, cs, it, rq);
+      printf("%d %d %.17g %.17g %.17g %.17g %.17g %.17g\n", ok ? 1 : 0, it, r[0], r[1], r[2], v[0], v[1], v[2]);
+    }
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def kepler_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    common = open(COMMON).read()
+    mvs = open(SRC).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    stumpff = re.search(r"__device__ __forceinline__ void stumpff23\(double z, double &c2, double &c3\) \{.*?\n\}\n",
+                        mvs, re.S).group(0)
+    kep = mvs[mvs.index("struct KepConst {"):mvs.index("// ---------------------------------------------------------------- coordinate maps")]
+    prog = ("#include <cmath>\n#include <cstdio>\nusing std::fabs; using std::fma; using std::sqrt; using std::fmax;\n"
+            "#define __device__\n#define __forceinline__ inline\n#define __noinline__\n"
+            "static inline bool __all_sync(unsigned, bool p) { return p; }\n"
+            "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n"
+            "namespace swarm {\n" + f64k + stumpff + kep + "}\n" + KEPLER_MAIN)
+    d = tmp_path_factory.mktemp("kepler")
+    (d / "k.cpp").write_text(prog)
+    exe = d / "k"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe), str(d / "k.cpp")], check=True)
+    return exe
+
+
+def kepler_exact(mu, r0, v0, t):
+    """Two-body state after time t: Kepler's equation solved in 40-digit arithmetic."""
+    mp.mp.dps = 40
+    r0 = [mp.mpf(x) for x in r0]
+    v0 = [mp.mpf(x) for x in v0]
+    mu = mp.mpf(mu)
+    t = mp.mpf(t)
+    rn = mp.sqrt(sum(x * x for x in r0))
+    v2 = sum(x * x for x in v0)
+    a = 1 / (2 / rn - v2 / mu)
+    rv = sum(x * y for x, y in zip(r0, v0))
+    if a > 0:
+        n = mp.sqrt(mu / a ** 3)
+        ecosE, esinE = 1 - rn / a, rv / mp.sqrt(mu * a)
+        # solve for the change of eccentric anomaly dE: n t = dE - ecosE sin dE + esinE (1 - cos dE)
+        dE = mp.findroot(lambda x: x - ecosE * mp.sin(x) + esinE * (1 - mp.cos(x)) - n * t, n * t)
+        f = 1 - a / rn * (1 - mp.cos(dE))
+        g = t - (dE - mp.sin(dE)) / n
+        r = [f * x + g * y for x, y in zip(r0, v0)]
+        rr = mp.sqrt(sum(x * x for x in r))
+        fd = -mp.sqrt(mu * a) / (rr * rn) * mp.sin(dE)
+        gd = 1 - a / rr * (1 - mp.cos(dE))
+    else:
+        an = -a
+        n = mp.sqrt(mu / an ** 3)
+        ecoshF, esinhF = 1 + rn / an, rv / mp.sqrt(mu * an)
+        dF = mp.findroot(lambda x: -x + ecoshF * mp.sinh(x) + esinhF * (mp.cosh(x) - 1) - n * t, mp.asinh(n * t))
+        f = 1 - an / rn * (mp.cosh(dF) - 1)
+        g = t - (mp.sinh(dF) - dF) / n
+        r = [f * x + g * y for x, y in zip(r0, v0)]
+        rr = mp.sqrt(sum(x * x for x in r))
+        fd = -mp.sqrt(mu * an) / (rr * rn) * mp.sinh(dF)
+        gd = 1 - an / rr * (mp.cosh(dF) - 1)
+    v = [fd * x + gd * y for x, y in zip(r0, v0)]
+    return [float(x) for x in r], [float(x) for x in v]
+
+
+def drift_run(exe, mu, h, steps, r, v):
+    line = " ".join([repr(float(mu)), repr(float(h)), str(int(steps))] + [repr(float(x)) for x in [*r, *v]])
+    out = subprocess.run([str(exe)], input=line, capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = [list(map(float, l.split())) for l in out if l.strip()]
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("e", [0.0, 0.05, 0.3, 0.9])
+def test_kepler_drift_elliptic_host(kepler_exe, e):
+    # the kernel's drift (extrapolated start, quadratic stop, Taylor finalize) over 60 steps
+    # of 1/20 orbit against Kepler's equation: the state to 1e-13, two or three Newton
+    # iterations per step once the extrapolation has three solutions
+    mu, a = 1.0 + 1e-3, 1.3
+    r0 = [a * (1 - e), 0.0, 0.01]
+    v0 = [0.0, float(np.sqrt(mu * (1 + e) / (a * (1 - e)))), 0.002]
+    T = 2 * np.pi * np.sqrt(a ** 3 / mu)
+    h = T / 20
+    rows = drift_run(kepler_exe, mu, h, 60, r0, v0)
+    assert np.all(rows[:, 0] == 1)
+    for s in (0, 9, 19, 39, 59):
+        rx, vx = kepler_exact(mu, r0, v0, h * (s + 1))
+        assert np.max(np.abs(rows[s, 2:5] - rx)) <= 1e-13 * np.max(np.abs(rx)) * (s + 1)
+        assert np.max(np.abs(rows[s, 5:8] - vx)) <= 1e-13 * np.max(np.abs(vx)) * (s + 1)
+    if e <= 0.3:
+        assert rows[3:, 1].max() <= 3
+
+
+def test_kepler_drift_hyperbolic_host(kepler_exe):
+    mu = 1.0
+    r0 = [1.0, 0.0, 0.0]
+    v0 = [0.0, 1.8, 0.1]  # v^2 > 2 mu / r: unbound
+    h = 0.05
+    rows = drift_run(kepler_exe, mu, h, 40, r0, v0)
+    assert np.all(rows[:, 0] == 1)
+    rx, vx = kepler_exact(mu, r0, v0, h * 40)
+    assert np.max(np.abs(rows[-1, 2:5] - rx)) <= 1e-12 * np.max(np.abs(rx))
+    assert np.max(np.abs(rows[-1, 5:8] - vx)) <= 1e-12 * np.max(np.abs(vx))
