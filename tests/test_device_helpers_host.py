@@ -238,3 +238,94 @@ def test_kepler_drift_hyperbolic_host(kepler_exe):
     rx, vx = kepler_exact(mu, r0, v0, h * 40)
     assert np.max(np.abs(rows[-1, 2:5] - rx)) <= 1e-12 * np.max(np.abs(rx))
     assert np.max(np.abs(rows[-1, 5:8] - vx)) <= 1e-12 * np.max(np.abs(vx))
+
+
+HERMITE = os.path.join(os.path.dirname(SRC), "hermite.cuh")
+
+REL_MAIN = r"""
+#include <random>
+using namespace swarm;
+static double relmax(const double (&a)[3][3], const double (&b)[3][3], int i0) {
+  double e = 0.0, s = 0.0;
+  for (int i = i0; i < 3; i++) for (int c = 0; c < 3; c++) { e = fmax(e, fabs(a[i][c] - b[i][c])); s = fmax(s, fabs(b[i][c])); }
+  return e / s;
+}
+int main() {
+  const F64k k = {0.0, -1.0, 1.0};
+  std::mt19937_64 g(7);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  double worst_acc = 0, worst_jerk = 0, worst_round = 0, worst_cached = 0, worst_fallback = 0;
+  for (int trial = 0; trial < 2000; trial++) {
+    double m[3] = {1.0, 1e-3 * (1.5 + U(g)), 1e-3 * (1.5 + U(g))};
+    if (trial % 4 == 0) { m[1] = 0.5 + 0.3 * U(g); m[2] = 0.5 + 0.3 * U(g); }  // comparable masses
+    double x[3][3], v[3][3];
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) { x[i][c] = (i ? 1.5 * i : 0.0) * (c == 0) + 0.4 * U(g); v[i][c] = 0.5 * U(g); }
+    double a[3][3], j[3][3], q2[3], d2[3][3];
+    spl_accjerk<3>(k, x, v, m, a, j, q2, d2);               // inertial
+    double X[3][3], V[3][3], Minv, Xc[3], Vc[3];
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) { X[i][c] = x[i][c]; V[i][c] = v[i][c]; }
+    spl_to_rel<3>(m, X, V, Minv, Xc, Vc);
+    double A[3][3], J[3][3];
+    spl_accjerk_rel<3>(k, X, V, m, A, J, q2, d2);
+    double ai[3][3], ji[3][3];                               // inertial from relative
+    for (int c = 0; c < 3; c++) { ai[0][c] = A[0][c]; ji[0][c] = J[0][c];
+      for (int i = 1; i < 3; i++) { ai[i][c] = A[i][c] + A[0][c]; ji[i][c] = J[i][c] + J[0][c]; } }
+    worst_acc = fmax(worst_acc, relmax(ai, a, 0));
+    worst_jerk = fmax(worst_jerk, relmax(ji, j, 0));
+    double xo[3][3], vo[3][3];
+    spl_from_rel<3>(m, X, V, Minv, Xc, Vc, xo, vo);
+    worst_round = fmax(worst_round, fmax(relmax(xo, x, 0), relmax(vo, v, 0)));
+    // cached 1/|d|: fill at X, evaluate at a corrector-sized move and at a large one
+    for (int big = 0; big < 2; big++) {
+      RhoCache<3> rc;
+      double A1[3][3], J1[3][3], A2[3][3], J2[3][3], Y[3][3];
+      spl_accjerk_rel_cached<3, true>(k, X, V, m, A1, J1, q2, d2, rc);
+      for (int i = 1; i < 3; i++) for (int c = 0; c < 3; c++) Y[i][c] = X[i][c] * (1.0 + (big ? 1e-3 : 1e-10) * U(g));
+      spl_accjerk_rel_cached<3, false>(k, Y, V, m, A2, J2, q2, d2, rc);
+      spl_accjerk_rel<3>(k, Y, V, m, A1, J1, q2, d2);        // reference: rsqrt
+      double e = fmax(relmax(A2, A1, 1), relmax(J2, J1, 1));
+      if (big) worst_fallback = fmax(worst_fallback, e); else worst_cached = fmax(worst_cached, e);
+    }
+  }
+  printf("%.3e %.3e %.3e %.3e %.3e\n", worst_acc, worst_jerk, worst_round, worst_cached, worst_fallback);
+  return 0;
+}
+"""
+
+
+def test_star_relative_evaluation_host():
+    # the system-per-lane Hermite kernel's relative-coordinate evaluation (spl_accjerk_rel,
+    # its cached-1/|d| variant and the frame maps), compiled as host code: A_k + A_0 and
+    # J_k + J_0 equal the inertial a_k, j_k of the same kernel file's inertial evaluation,
+    # the frame maps round-trip, and the series-refined 1/|d| (corrector-sized moves) and
+    # its rsqrt fallback (large moves) agree with rsqrt
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import tempfile
+    common = open(COMMON).read()
+    herm = open(HERMITE).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    pair = re.search(r"__device__ __forceinline__ void pair_geom\(.*?\n\}\n", herm, re.S).group(0)
+    inert = re.search(r"template <int N>\n__device__ __forceinline__ void spl_accjerk\(.*?\n\}\n", herm, re.S).group(0)
+    rel = herm[herm.index("// Coordinates relative to body 0"):
+               herm.index("template <int N>\n__device__ __forceinline__ void spl_energy(")]
+    prog = ("#include <cmath>\n#include <cstdio>\n#include <cstring>\n"
+            "using std::fabs; using std::fma; using std::sqrt; using std::fmax;\n"
+            "#define __device__\n#define __forceinline__ inline\n#define __noinline__\n"
+            "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n"
+            "static inline int __double2hiint(double x) { long long b; std::memcpy(&b, &x, 8); return (int)(b >> 32); }\n"
+            "namespace swarm {\n" + f64k + pair + inert + rel + "}\n" + REL_MAIN)
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "r.cpp"), "w") as f:
+        f.write(prog)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-Wno-unknown-pragmas", "-o",
+                    os.path.join(d, "r"), os.path.join(d, "r.cpp")], check=True)
+    acc, jerk, rnd, cached, fallback = map(float, subprocess.run([os.path.join(d, "r")], capture_output=True,
+                                                                 text=True, check=True).stdout.split())
+    print("relative-frame evaluation:", acc, jerk, rnd, cached, fallback)
+    assert acc <= 1e-14 and jerk <= 1e-14, (acc, jerk)
+    assert rnd <= 1e-15, rnd
+    # the series and rsqrt round differently: a few units in the last place of 1/|d|,
+    # relative to the largest acceleration or jerk of the system
+    assert cached <= 1e-14 and fallback <= 1e-15, (cached, fallback)
