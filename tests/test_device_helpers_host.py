@@ -329,3 +329,87 @@ def test_star_relative_evaluation_host():
     # the series and rsqrt round differently: a few units in the last place of 1/|d|,
     # relative to the largest acceleration or jerk of the system
     assert cached <= 1e-14 and fallback <= 1e-15, (cached, fallback)
+
+
+RK_MAIN = r"""
+using namespace swarm;
+int main() {
+  // per line: m0 m1 m2, x (9), v (9), h; prints the 5th-order x, v and the error vectors
+  // (position, velocity) of all bodies in inertial coordinates
+  const F64k k = {0.0, -1.0, 1.0};
+  double m[3], x[3][3], v[3][3], h;
+  while (scanf("%lf %lf %lf", &m[0], &m[1], &m[2]) == 3) {
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) if (scanf("%lf", &x[i][c]) != 1) return 1;
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) if (scanf("%lf", &v[i][c]) != 1) return 1;
+    if (scanf("%lf", &h) != 1) return 1;
+    double Minv, Xc[3], Vc[3], a1[3][3], q2[3], d2[3][3], x5[3][3], v5[3][3], ex[3][3], ev[3][3];
+    spl_to_rel<3>(m, x, v, Minv, Xc, Vc);
+    spl_acc_rel<3>(k, x, m, a1, q2, d2);
+    spl_rkck_step<3, true>(k, x, v, a1, m, Minv, h, x5, v5, ex, ev);
+    for (int c = 0; c < 3; c++) Xc[c] = fma(h, Vc[c], Xc[c]);
+    double xo[3][3], vo[3][3];
+    spl_from_rel<3>(m, x5, v5, Minv, Xc, Vc, xo, vo);
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) printf("%.17g ", xo[i][c]);
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) printf("%.17g ", vo[i][c]);
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) printf("%.17g ", i ? ex[i][c] + ex[0][c] : ex[0][c]);
+    for (int i = 0; i < 3; i++) for (int c = 0; c < 3; c++) printf("%.17g ", i ? ev[i][c] + ev[0][c] : ev[0][c]);
+    printf("\n");
+  }
+  return 0;
+}
+"""
+
+
+def test_runge_kutta_relative_step_host():
+    # the system-per-lane Runge-Kutta kernel's step (star-relative coordinates, Nystrom
+    # stages, inertial error vectors rebuilt from the relative ones), compiled as host
+    # code, against the oracle's Cash-Karp step in inertial coordinates
+    import oracle as O
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import tempfile
+    common = open(COMMON).read()
+    herm = open(HERMITE).read()
+    rk = open(RK).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    frames = herm[herm.index("// Coordinates relative to body 0"):
+                  herm.index("// Acceleration and jerk of bodies k = 1..N-1 relative to body 0")]
+    ck = re.search(r"struct CK \{.*?\n\};\n", rk, re.S).group(0)
+    ckn = re.search(r"struct CKN \{.*?\n\};\n", rk, re.S).group(0)
+    acc = re.search(r"template <int N>\n__device__ __forceinline__ void spl_acc_rel\(.*?\n\}\n", rk, re.S).group(0)
+    step = re.search(r"template <int N, bool E>\n__device__ __forceinline__ void spl_rkck_step\(.*?\n\}\n", rk,
+                     re.S).group(0)
+    prog = ("#include <cmath>\n#include <cstdio>\nusing std::fabs; using std::fma; using std::sqrt; using std::fmax;\n"
+            "#define __device__\n#define __forceinline__ inline\n#define __noinline__\n"
+            "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n"
+            "namespace swarm {\n" + f64k + frames + ck + ckn + acc + step + "}\n" + RK_MAIN)
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "k.cpp"), "w") as f:
+        f.write(prog)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-Wno-unknown-pragmas", "-o",
+                    os.path.join(d, "k"), os.path.join(d, "k.cpp")], check=True)
+    rng = np.random.default_rng(11)
+    cases, lines = [], []
+    for t in range(40):
+        m = np.array([1.0, *rng.uniform(1e-5, 1e-3, 2)]) if t % 4 else rng.uniform(0.3, 1.0, 3)
+        x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [-2.2, 0.4, 0.0]]) + 0.05 * rng.standard_normal((3, 3))
+        v = np.array([[0.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, -0.65, 0.02]]) + 0.02 * rng.standard_normal((3, 3))
+        h = float(rng.uniform(0.05, 0.15))  # error vectors well above the oracle's cancellation noise
+        cases.append((m, x, v, h))
+        lines.append(" ".join(repr(float(q)) for q in [*m, *x.ravel(), *v.ravel(), h]))
+    out = subprocess.run([os.path.join(d, "k")], input="\n".join(lines), capture_output=True, text=True,
+                         check=True).stdout.strip().split("\n")
+    worst = np.zeros(4)
+    for (m, x, v, h), row in zip(cases, out):
+        r = np.array(list(map(float, row.split()))).reshape(4, 3, 3)
+        xo, vo, _, err = O.rkck_step(m, x, v, h)
+        for q, ref in enumerate((xo, vo, err[:3], err[3:])):
+            worst[q] = max(worst[q], np.max(np.abs(r[q] - ref)) / np.max(np.abs(ref)))
+        assert np.max(np.abs(r[0] - xo)) <= 1e-14 * np.max(np.abs(xo))
+        assert np.max(np.abs(r[1] - vo)) <= 1e-14 * np.max(np.abs(vo))
+        # the oracle's error vector carries the cancellation of the stage velocities; the
+        # kernel's carries none
+        assert np.max(np.abs(r[2] - err[:3])) <= 1e-6 * np.max(np.abs(err[:3]))
+        assert np.max(np.abs(r[3] - err[3:])) <= 1e-6 * np.max(np.abs(err[3:]))
+    print("relative Runge-Kutta step against the oracle:", worst)
