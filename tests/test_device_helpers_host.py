@@ -413,3 +413,75 @@ def test_runge_kutta_relative_step_host():
         assert np.max(np.abs(r[2] - err[:3])) <= 1e-6 * np.max(np.abs(err[:3]))
         assert np.max(np.abs(r[3] - err[3:])) <= 1e-6 * np.max(np.abs(err[3:]))
     print("relative Runge-Kutta step against the oracle:", worst)
+
+
+MONITOR_MAIN = r"""
+using namespace swarm;
+int main() {
+  // per line: ce mi mj m0 d2 q2i q2j -> close_encounter(d2, hill_kc(...), q2i, q2j)
+  const F64k k = {0.0, -1.0, 1.0};
+  double ce, mi, mj, m0, d2, qi, qj;
+  while (scanf("%lf %lf %lf %lf %lf %lf %lf", &ce, &mi, &mj, &m0, &d2, &qi, &qj) == 7)
+    printf("%d\n", close_encounter(k, d2, hill_kc(ce, mi, mj, m0), qi, qj) ? 1 : 0);
+  // nonneg_lt against the FP64 order on non-negative values, including 0, subnormals, inf
+  const double vals[] = {0.0, 4.9e-324, 2.2e-308, 1e-300, 1e-20, 0.5, 1.0, 1.0000000000000002, 3.0, 1e300,
+                         1.7976931348623157e308, INFINITY};
+  int bad = 0;
+  for (double a : vals) for (double b : vals) bad += nonneg_lt(a, b) != (a < b);
+  printf("order %d\n", bad);
+  return 0;
+}
+"""
+
+
+def test_monitor_host():
+    # the monitor's close-encounter test (mutual Hill radius, with its square-root-free
+    # shortcut and integer compare) against the definition of the reading, evaluated in
+    # 40-digit arithmetic, on cases clustered at the boundary; and the integer order of
+    # non-negative doubles
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import tempfile
+    common = open(COMMON).read()
+    herm = open(HERMITE).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    lt = re.search(r"__device__ __forceinline__ bool nonneg_lt\(double a, double b\) \{.*?\n\}\n", common,
+                   re.S).group(0)
+    ce = re.search(r"__device__ __forceinline__ bool close_encounter\(.*?\n\}\n", herm, re.S).group(0)
+    kc = re.search(r"__device__ __forceinline__ double hill_kc\(.*?\n\}\n", herm, re.S).group(0)
+    prog = ("#include <cmath>\n#include <cstdio>\n#include <cstring>\n"
+            "using std::fabs; using std::fma; using std::sqrt; using std::cbrt;\n"
+            "#define __device__\n#define __forceinline__ inline\n"
+            "static inline long long __double_as_longlong(double x) { long long b; std::memcpy(&b, &x, 8); return b; }\n"
+            "namespace swarm {\n" + f64k + lt + ce + kc + "}\n" + MONITOR_MAIN)
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "m.cpp"), "w") as f:
+        f.write(prog)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", os.path.join(d, "m"),
+                    os.path.join(d, "m.cpp")], check=True)
+    rng = np.random.default_rng(3)
+    rows, want = [], []
+    mp.mp.dps = 40
+    for _ in range(3000):
+        cef, mi, mj = 3.0, 10 ** rng.uniform(-5, -3), 10 ** rng.uniform(-5, -3)
+        qi, qj = rng.uniform(0.5, 5.0, 2)
+        rh = float(((mp.mpf(mi) + mj) / 3) ** (mp.mpf(1) / 3) * (mp.mpf(qi) + qj) / 2)
+        dist = cef * rh * (1 + float(rng.choice([-1, 1])) * 10 ** rng.uniform(-12, -1))
+        if rng.uniform() < 0.1:
+            dist = float(rng.uniform(0.0, 10.0))
+        d2, q2i, q2j = dist * dist, qi * qi, qj * qj
+        rows.append(" ".join(repr(float(t)) for t in [cef, mi, mj, 1.0, d2, q2i, q2j]))
+        # the definition on the same (rounded) inputs: |d| < ce R_H, R_H = ((mi+mj)/3)^(1/3) (|Qi|+|Qj|)/2
+        R = ((mp.mpf(mi) + mp.mpf(mj)) / 3) ** (mp.mpf(1) / 3) * (mp.sqrt(mp.mpf(q2i)) + mp.sqrt(mp.mpf(q2j))) / 2
+        margin = abs(mp.sqrt(mp.mpf(d2)) - cef * R) / (cef * R)
+        want.append((mp.sqrt(mp.mpf(d2)) < cef * R, float(margin)))
+    out = subprocess.run([os.path.join(d, "m")], input="\n".join(rows), capture_output=True, text=True,
+                         check=True).stdout.strip().split("\n")
+    assert out[-1] == "order 0"
+    got = [s == "1" for s in out[:-1]]
+    for g, (w, margin) in zip(got, want):
+        # outside a few units of round-off from the boundary the kernel decides as the definition
+        if margin > 1e-14:
+            assert g == w, margin
+    assert sum(got) > 500 and sum(not g for g in got) > 500  # both outcomes exercised
