@@ -19,10 +19,8 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
                    "mvs_impl.cuh")
 
 
-@pytest.fixture(scope="module")
-def stumpff_exe(tmp_path_factory):
-    if shutil.which("g++") is None:
-        pytest.skip("no g++")
+def build_stumpff(d):
+    """Host build of the kernel's stumpff23 (from SRC) in directory d."""
     text = open(SRC).read()
     fn = re.search(r"__device__ __forceinline__ void stumpff23\(double z, double &c2, double &c3\) \{.*?\n\}\n",
                    text, re.S).group(0).replace("__device__ __forceinline__ ", "static ")
@@ -31,11 +29,18 @@ def stumpff_exe(tmp_path_factory):
             "  double z;\n"
             "  while (scanf(\"%lf\", &z) == 1) { double c2, c3; stumpff23(z, c2, c3); printf(\"%.17g %.17g\\n\", c2, c3); }\n"
             "  return 0;\n}\n")
-    d = tmp_path_factory.mktemp("stumpff")
-    (d / "s.cpp").write_text(prog)
-    exe = d / "s"
-    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-o", str(exe), str(d / "s.cpp")], check=True)
+    with open(os.path.join(d, "s.cpp"), "w") as f:
+        f.write(prog)
+    exe = os.path.join(d, "s")
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-o", exe, os.path.join(d, "s.cpp")], check=True)
     return exe
+
+
+@pytest.fixture(scope="module")
+def stumpff_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    return build_stumpff(str(tmp_path_factory.mktemp("stumpff")))
 
 
 def run(exe, zs):
@@ -65,19 +70,27 @@ def rel_err(exe, zs):
     return e2, e3
 
 
-def test_series_range(stumpff_exe):
+def check_series_range(exe):
     # the range the Kepler drift of 1/20-orbit steps meets: the series alone
     zs = np.concatenate([np.linspace(-0.25, 0.25, 201), [0.0, 1e-300, -1e-12, 0.099, 0.25, -0.25]])
-    e2, e3 = rel_err(stumpff_exe, zs)
+    e2, e3 = rel_err(exe, zs)
     assert e2 <= 3e-16 and e3 <= 3e-16, (e2, e3)
 
 
-def test_quartering_and_doubling(stumpff_exe):
+def check_quartering_and_doubling(exe):
     # elliptic arguments up to (2 pi)^2 (a whole orbit) and hyperbolic ones; near
     # z = (2 pi)^2, c2 is small against the terms of the doubling (7e-14 relative there)
     zs = np.concatenate([np.linspace(0.26, 39.0, 97), -np.linspace(0.26, 30.0, 60)])
-    e2, e3 = rel_err(stumpff_exe, zs)
+    e2, e3 = rel_err(exe, zs)
     assert e2 <= 3e-13 and e3 <= 3e-13, (e2, e3)
+
+
+def test_series_range(stumpff_exe):
+    check_series_range(stumpff_exe)
+
+
+def test_quartering_and_doubling(stumpff_exe):
+    check_quartering_and_doubling(stumpff_exe)
 
 
 def test_universal_identity(stumpff_exe):
@@ -141,10 +154,8 @@ int main() {
 """
 
 
-@pytest.fixture(scope="module")
-def kepler_exe(tmp_path_factory):
-    if shutil.which("g++") is None:
-        pytest.skip("no g++")
+def build_kepler(d):
+    """Host build of the kernel's kepler_drift (from COMMON and SRC) in directory d."""
     common = open(COMMON).read()
     mvs = open(SRC).read()
     f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
@@ -157,11 +168,18 @@ def kepler_exe(tmp_path_factory):
             "static inline bool __all_sync(unsigned, bool p) { return p; }\n"
             "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n"
             "namespace swarm {\n" + f64k + stumpff + kep + "}\n" + KEPLER_MAIN)
-    d = tmp_path_factory.mktemp("kepler")
-    (d / "k.cpp").write_text(prog)
-    exe = d / "k"
-    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe), str(d / "k.cpp")], check=True)
+    with open(os.path.join(d, "k.cpp"), "w") as f:
+        f.write(prog)
+    exe = os.path.join(d, "k")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe, os.path.join(d, "k.cpp")], check=True)
     return exe
+
+
+@pytest.fixture(scope="module")
+def kepler_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    return build_kepler(str(tmp_path_factory.mktemp("kepler")))
 
 
 def kepler_exact(mu, r0, v0, t):
@@ -208,8 +226,7 @@ def drift_run(exe, mu, h, steps, r, v):
     return np.array(rows)
 
 
-@pytest.mark.parametrize("e", [0.0, 0.05, 0.3, 0.9])
-def test_kepler_drift_elliptic_host(kepler_exe, e):
+def check_kepler_elliptic(kepler_exe, e):
     # the kernel's drift (extrapolated start, quadratic stop, Taylor finalize) over 60 steps
     # of 1/20 orbit against Kepler's equation: the state to 1e-13, two or three Newton
     # iterations per step once the extrapolation has three solutions
@@ -226,6 +243,11 @@ def test_kepler_drift_elliptic_host(kepler_exe, e):
         assert np.max(np.abs(rows[s, 5:8] - vx)) <= 1e-13 * np.max(np.abs(vx)) * (s + 1)
     if e <= 0.3:
         assert rows[3:, 1].max() <= 3
+
+
+@pytest.mark.parametrize("e", [0.0, 0.05, 0.3, 0.9])
+def test_kepler_drift_elliptic_host(kepler_exe, e):
+    check_kepler_elliptic(kepler_exe, e)
 
 
 def test_kepler_drift_hyperbolic_host(kepler_exe):
@@ -485,3 +507,66 @@ def test_monitor_host():
         if margin > 1e-14:
             assert g == w, margin
     assert sum(got) > 500 and sum(not g for g in got) > 500  # both outcomes exercised
+
+
+# Plausible mistakes planted in copies of the kernel sources: each must fail one of the
+# host checks above (the GPU parity tests are the gate for the kernels; these show that the
+# host checks are sharp enough to stand beside them).
+KERNEL_MUTANTS = [
+    ("nystrom_product_sign", "rkck_impl.cuh", "A62 = -805.0 / 4096.0", "A62 = 805.0 / 4096.0", "constants"),
+    ("error_weight", "rkck_impl.cuh", "E5 = 277.0 / 114688.0", "E5 = 277.0 / 114689.0", "constants"),
+    ("stumpff_term", "mvs_impl.cuh", "c2 = fma(z, c2, 1.0 / 40320.0);", "c2 = fma(z, c2, 1.0 / 40321.0);", "series"),
+    ("stumpff_doubling", "mvs_impl.cuh", "c3 = 0.25 * fma(c0, c3, c2);", "c3 = 0.5 * fma(c0, c3, c2);", "doubling"),
+    ("kepler_taylor_sign", "mvs_impl.cuh", "const double U2n = fma(U0, d2h, fma(-U1, dx, U2));",
+     "const double U2n = fma(U0, d2h, fma(U1, dx, U2));", "kepler"),
+    ("kepler_fdot_sign", "mvs_impl.cuh", "kmul(k, kmul(k, -K.smu, U1), kmul(k, rinv0, rinv))",
+     "kmul(k, kmul(k, K.smu, U1), kmul(k, rinv0, rinv))", "kepler"),
+    ("relative_indirect_sign", "hermite.cuh", "A[k][c] = fma(-m0s[k], X[k][c], -IA[c]);",
+     "A[k][c] = fma(-m0s[k], X[k][c], IA[c]);", "relative"),
+    ("series_refinement_sign", "hermite.cuh", "fma(0.375, del[i][k], -0.5)", "fma(0.375, del[i][k], 0.5)", "relative"),
+    ("rk_body0_error_sign", "rkck_impl.cuh", "ex[0][c] = kmul(k, -sx, Minv);", "ex[0][c] = kmul(k, sx, Minv);",
+     "runge_kutta"),
+    ("rk_indirect_sign", "rkck_impl.cuh", "A[k][c] = fma(-m0s[k], X[k][c], -A[0][c]);",
+     "A[k][c] = fma(-m0s[k], X[k][c], A[0][c]);", "runge_kutta"),
+    ("hill_factor", "hermite.cuh", "double k = cbrt((mi + mj) / (3.0 * m0));", "double k = cbrt((mi + mj) / (2.0 * m0));",
+     "monitor"),
+    ("encounter_shortcut", "hermite.cuh", "kmul(k, kmul(k, 2.0, kc), t)", "kmul(k, kmul(k, 1.0, kc), t)", "monitor"),
+]
+
+
+@pytest.mark.parametrize("name,fname,old,new,check", KERNEL_MUTANTS, ids=[m[0] for m in KERNEL_MUTANTS])
+def test_host_checks_catch_planted_kernel_mistakes(name, fname, old, new, check, tmp_path, monkeypatch):
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import test_rkck_constants as rc
+    csrc = os.path.dirname(SRC)
+    for f in ("common.cuh", "hermite.cuh", "mvs_impl.cuh", "rkck_impl.cuh"):
+        text = open(os.path.join(csrc, f)).read()
+        if f == fname:
+            assert old in text, (name, "the planted text is not in the source")
+            text = text.replace(old, new, 1)
+        (tmp_path / f).write_text(text)
+    here = __import__(__name__)
+    monkeypatch.setattr(here, "SRC", str(tmp_path / "mvs_impl.cuh"))
+    monkeypatch.setattr(here, "RK", str(tmp_path / "rkck_impl.cuh"))
+    monkeypatch.setattr(here, "COMMON", str(tmp_path / "common.cuh"))
+    monkeypatch.setattr(here, "HERMITE", str(tmp_path / "hermite.cuh"))
+    monkeypatch.setattr(rc, "SRC", str(tmp_path / "rkck_impl.cuh"))
+    with pytest.raises(AssertionError):
+        if check == "constants":
+            rc.test_stage_weights_and_errors_match_the_tableau()
+            rc.test_nystrom_products_match_the_tableau()
+        elif check == "series":
+            check_series_range(build_stumpff(str(tmp_path)))
+        elif check == "doubling":
+            check_quartering_and_doubling(build_stumpff(str(tmp_path)))
+        elif check == "kepler":
+            exe = build_kepler(str(tmp_path))
+            for e in (0.05, 0.3):
+                check_kepler_elliptic(exe, e)
+        elif check == "relative":
+            test_star_relative_evaluation_host()
+        elif check == "runge_kutta":
+            test_runge_kutta_relative_step_host()
+        elif check == "monitor":
+            test_monitor_host()
