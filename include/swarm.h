@@ -88,7 +88,9 @@ enum swarm_mapping {
 
 /* options for swarm_set_option */
 enum swarm_option {
-  SWARM_OPT_MAPPING = 1,        /* enum swarm_mapping, all bins (default AUTO) */
+  SWARM_OPT_MAPPING = 1,        /* enum swarm_mapping, all bins (default AUTO); the Runge-Kutta
+                                    integrators choose their own (system per lane for n <= 3,
+                                    body per lane above) */
   SWARM_OPT_N_CORR = 2,         /* Hermite corrector passes, 1..8 (default 2, Sec. 2.2.1) */
   SWARM_OPT_LOG_INTERVAL = 3,   /* steps between energy/angular-momentum records, 0 = off */
   SWARM_OPT_LOG_CAPACITY = 4,   /* records kept per system (ring of this size), 0..65536 */

@@ -582,7 +582,9 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   int ctas = e->ctas_per_sm;
   for (size_t i = 0; i < e->bins.size(); i++) {
     int m = e->mapping;
-    if (rkck_family(integrator)) m = SWARM_MAP_BODY_PER_LANE;  // the only Runge-Kutta mapping
+    // Runge-Kutta: one kernel per n that picks its own layout (system per lane for n <= 3,
+    // body per lane above); the body-per-lane entry sizes its grid
+    if (rkck_family(integrator)) m = SWARM_MAP_BODY_PER_LANE;
     if (e->bins[i].n >= kWideMinN) {  // one system per warp, run-time n
       maps[i] = kMapWide;
       continue;
