@@ -570,3 +570,51 @@ def test_host_checks_catch_planted_kernel_mistakes(name, fname, old, new, check,
             test_runge_kutta_relative_step_host()
         elif check == "monitor":
             test_monitor_host()
+
+
+COEF_MAIN = r"""
+using namespace swarm;
+int main() {
+  double h;
+  const F64k k = {0.0, -1.0, 1.0};
+  while (scanf("%lf", &h) == 1) {
+    HCoef c = hcoef(h), d = hcoef(k, h);
+    PCoef p = pcoef(h);
+    printf("%.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g\n", c.h, c.h2_2, c.h3_6,
+           c.hh, c.h2_12, d.h2_2, d.h3_6, d.hh, d.h2_12, p.pa, p.pj, p.ca, p.cj);
+  }
+  return 0;
+}
+"""
+
+
+def test_step_coefficients_host():
+    # the Hermite step's coefficients (Eq. 3 predictor h, h^2/2, h^3/6; the time-symmetric
+    # corrector's h/2, h^2/12; the printed Eq. 4 form with 3/20: -3h^2/20, -7h^3/60, 3h^2/20,
+    # -h^3/30), both the plain and the DFMA-form builders, against exact fractions
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    import tempfile
+    from fractions import Fraction as Fr
+    common = open(COMMON).read()
+    herm = open(HERMITE).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    coef = herm[herm.index("// Coefficients of one step of length h."):herm.index("__device__ __forceinline__ HCoef hsel(")]
+    prog = ("#include <cmath>\n#include <cstdio>\nusing std::fma;\n#define __device__\n#define __forceinline__ inline\n"
+            "namespace swarm {\n" + f64k + coef + "}\n" + COEF_MAIN)
+    d = tempfile.mkdtemp()
+    with open(os.path.join(d, "c.cpp"), "w") as f:
+        f.write(prog)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", os.path.join(d, "c"),
+                    os.path.join(d, "c.cpp")], check=True)
+    hs = [2 * np.pi * 1e-3, -2 * np.pi * 1e-3, 0.05, 1e-7, 3.0]
+    out = subprocess.run([os.path.join(d, "c")], input="\n".join(repr(h) for h in hs), capture_output=True, text=True,
+                         check=True).stdout.strip().split("\n")
+    for h, row in zip(hs, out):
+        v = [float(t) for t in row.split()]
+        H = Fr(h)
+        want = [H, H * H / 2, H ** 3 / 6, H / 2, H * H / 12, H * H / 2, H ** 3 / 6, H / 2, H * H / 12,
+                -Fr(3, 20) * H * H, -Fr(7, 60) * H ** 3, Fr(3, 20) * H * H, -Fr(1, 30) * H ** 3]
+        for got, w in zip(v, want):
+            assert abs(Fr(got) - w) <= abs(w) * Fr(4, 2 ** 53), (h, got, float(w))
