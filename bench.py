@@ -281,10 +281,10 @@ def secondary(S, torch, stream):
                "kepler_iterations": st["kepler_iterations"]}
         if outcome:
             # stop outcomes, |dE/E| of the systems that reached t_end, Newton iterations per planet drift
-            names = ["active", "done", "close_encounter", "ejected", "kepler_noconv", "nonfinite"]
-            cnt = np.bincount(status, minlength=6)
+            names = ["active", "done", "close_encounter", "ejected", "kepler_noconv", "nonfinite", "span_limit"]
+            cnt = np.bincount(status, minlength=len(names))
             dE = np.abs(E1 / E0 - 1.0)[status == 1]
-            out["status_counts"] = {names[k]: int(cnt[k]) for k in range(6)}
+            out["status_counts"] = {names[k]: int(cnt[k]) for k in range(len(names))}
             if len(dE):
                 out["energy_error_done"] = {"p50": float(np.percentile(dE, 50)), "p90": float(np.percentile(dE, 90)),
                                             "max": float(dE.max())}
@@ -542,6 +542,13 @@ def ncu_case(name):
     elif name == "ragged":
         ens = ics.ragged(65536, seed=3)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 2, S.HERMITE4, DT
+    elif name.startswith("ragged_bin"):  # one body count of the ragged set (default n = 13), 100 steps
+        import numpy as np
+
+        n = int(name[len("ragged_bin"):] or 13)
+        full = ics.ragged(65536, seed=3)
+        ens = ics.subset(full, np.flatnonzero(np.asarray(full["n_body"]) == n))
+        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 100, S.HERMITE4, DT
     elif name == "rkck":
         ens = ics.three_body(N_SYS, seed=2)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 50, S.RKCK, DT
@@ -575,7 +582,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--ncu-case", choices=["hermite", "hermite_bpl", "plain", "mvs", "ragged", "rkck", "wide", "hermite_adaptive", "rkck_adaptive"])
+    ap.add_argument("--ncu-case", help="hermite, hermite_bpl, plain, mvs, ragged, ragged_bin<n>, rkck, wide, "
+                    "hermite_adaptive or rkck_adaptive")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)

@@ -74,7 +74,10 @@ enum swarm_sys_status {
   SWARM_SYS_CLOSE_ENCOUNTER = 2, /* two planets closer than ce_factor mutual Hill radii */
   SWARM_SYS_EJECTED = 3,         /* a planet farther than eject_radius from the central body */
   SWARM_SYS_KEPLER_NOCONV = 4,   /* a Kepler drift did not converge in 50 Newton steps */
-  SWARM_SYS_NONFINITE = 5        /* a position or velocity became NaN or infinite */
+  SWARM_SYS_NONFINITE = 5,       /* a position or velocity became NaN or infinite */
+  SWARM_SYS_SPAN_LIMIT = 6       /* allocation-free entry point only: the call asked this system
+                                    for more than 2e9 fixed steps; it was not advanced (the other
+                                    entry points reject such a call as a whole) */
 };
 
 /* thread mappings a bin of equal-n systems can run with (Sec. 4.1 work models) */
@@ -279,14 +282,18 @@ int swarm_fp64_peak(double seconds, void *cuda_stream, double *flops);
  * s_pad.  Mapping: a system per lane for n <= 3, a body per lane otherwise (fixed; the
  * autotuner is not used because it allocates).  Limit: at most 65520 work units, i.e.
  * 65520*32 systems for n <= 3 and 65520*floor(32/n) systems otherwise; larger ensembles
- * get SWARM_EINVAL with a message in swarm_last_error().
+ * get SWARM_EINVAL with a message in swarm_last_error().  Time span: at most 2e9 fixed
+ * steps per system and call; since the systems' times are on the device, a runnable
+ * system whose |t_end - t|/|dt| is larger is not advanced and gets status
+ * SWARM_SYS_SPAN_LIMIT (the call still returns SWARM_OK).
  *
  * The call enqueues its kernels on cuda_stream and returns; read the results after
- * synchronizing that stream.  The first call on a device looks up the device address
- * of the array (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array and each call resets its
- * counter, so calls whose kernels overlap on the GPU (other streams, other host
- * threads) race: serialize them. */
+ * synchronizing that stream.  Every call looks up the device address of the array
+ * (cudaGetSymbolAddress, with the calling thread's current device); the first call on a
+ * device also loads the library's device code there, so make that first call before any
+ * stream capture.  All calls share the one array and each call resets its counter, so
+ * calls whose kernels overlap on the GPU (other streams, other host threads) race:
+ * serialize them. */
 int swarm_hermite_integrate_noalloc(int32_t n, int32_t n_sys, int32_t s_pad, double *d_x, double *d_v,
                                     const double *d_m, double *d_t, int32_t *d_status, double t_end, double dt,
                                     double ce_hill_factor, double eject_radius, void *cuda_stream);

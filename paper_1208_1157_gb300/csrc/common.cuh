@@ -83,8 +83,15 @@ __device__ __forceinline__ bool nonneg_lt(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
+// Most fixed steps one call may ask of a system (below 2^31, so a step count is exact in
+// an int).  Every entry point rejects longer spans before launching: swarm_integrate and
+// swarm_server_submit on the host, the allocation-free entry point per system on the
+// device (status SWARM_SYS_SPAN_LIMIT).
+constexpr double kMaxCallSteps = 2.0e9;
+
 // Per-system step plan of Algorithm 1 with a shortened last step: N = round(D) when
-// D = (t_end - t)/dt is within 1e-9 of an integer, else ceil(D).
+// D = (t_end - t)/dt is within 1e-9 of an integer, else ceil(D).  A span beyond
+// kMaxCallSteps (rejected before launch, see above) plans no step instead of overflowing.
 struct StepPlan {
   long long N;
   double h_last;
@@ -93,7 +100,7 @@ struct StepPlan {
 __device__ __forceinline__ StepPlan plan_steps(double t, double t_end, double dt) {
   StepPlan p;
   double D = (t_end - t) / dt;
-  if (!(D > 1e-9)) {
+  if (!(D > 1e-9) || !(D <= kMaxCallSteps)) {
     p.N = 0;
     p.h_last = dt;
     p.exact = 1;

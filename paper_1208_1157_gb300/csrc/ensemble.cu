@@ -763,7 +763,7 @@ static int integrate_impl(swarm_ensemble *e, double t_end, int integrator, doubl
     return fail(SWARM_EINVAL, "unknown integrator %d", integrator);
   if (!(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t_end)) return fail(SWARM_EINVAL, "dt must be finite and non-zero, t_end finite");
   double span = std::max(std::fabs(t_end - e->t_lo), std::fabs(t_end - e->t_hi)) / std::fabs(dt);
-  if (!adaptive(integrator) && span > 2.0e9) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
+  if (!adaptive(integrator) && !(span <= kMaxCallSteps)) return fail(SWARM_EINVAL, "more than 2e9 steps in one call");
   if (e->mapping == SWARM_MAP_PLAIN_PER_STEP && (integrator != SWARM_HERMITE4 || e->corr_form))
     return fail(SWARM_EINVAL, "the plain per-step baseline exists for the fixed-step time-symmetric Hermite only");
   StepParams P = make_params(e, t_end, integrator, dt);
@@ -811,7 +811,7 @@ extern "C" int swarm_set_state(swarm_ensemble *e, const double *pos, const doubl
   }
   if (status)
     for (int s = 0; s < e->n_sys; s++)
-      if (status[s] < 0 || status[s] > SWARM_SYS_NONFINITE) return fail(SWARM_EINVAL, "status[%d] invalid", s);
+      if (status[s] < 0 || status[s] > SWARM_SYS_SPAN_LIMIT) return fail(SWARM_EINVAL, "status[%d] invalid", s);
   if ((rc = upload_state(e, pos, vel, nullptr, time, status))) return rc;
   CK(cudaStreamSynchronize(e->stream));
   return SWARM_OK;

@@ -6,7 +6,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -23,18 +22,19 @@ constexpr size_t kMaxUnits = (kScratchBytes - kHeaderBytes) / sizeof(int4);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device, looked up once per device with that device
-// current (host code cannot use the symbol itself as a device pointer).
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
+// the bin descriptor's slot in the header
+static_assert(sizeof(swarm::BinView) <= 128 && alignof(swarm::BinView) <= 128, "BinView outgrew its header slot");
 
 int reject(int rc, const char *msg) {
   swarm::set_last_error(msg);  // readable through swarm_last_error()
   return rc;
 }
 
-__global__ void noalloc_setup_kernel(unsigned char *scratch, swarm::BinView bin, int units, int mapping) {
+// Writes the bin descriptor, zeroes the work counter and fills the work list; a runnable
+// system whose span asks for more than 2e9 fixed steps is marked SWARM_SYS_SPAN_LIMIT, so
+// the integrator leaves it alone (its step count would not fit the kernels' int).
+__global__ void noalloc_setup_kernel(unsigned char *scratch, swarm::BinView bin, int units, int mapping,
+                                     double t_end, double dt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *reinterpret_cast<swarm::BinView *>(scratch) = bin;
@@ -42,6 +42,8 @@ __global__ void noalloc_setup_kernel(unsigned char *scratch, swarm::BinView bin,
   }
   int4 *work = reinterpret_cast<int4 *>(scratch + kHeaderBytes);
   if (i < units) work[i] = make_int4(0, i, mapping, bin.n);
+  if (i < bin.S && bin.status[i] <= SWARM_SYS_DONE && !(fabs((t_end - bin.t[i]) / dt) <= swarm::kMaxCallSteps))
+    bin.status[i] = SWARM_SYS_SPAN_LIMIT;
 }
 
 }  // namespace
@@ -65,18 +67,17 @@ extern "C" int swarm_hermite_integrate_noalloc(int32_t n, int32_t n_sys, int32_t
     return reject(SWARM_EINVAL, "ensemble too large for the fixed 1 MiB work list of the allocation-free entry point");
 
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return reject(SWARM_ECUDA, "cudaGetDevice failed or device index out of range");
+  if (cudaGetDevice(&dev) != cudaSuccess) return reject(SWARM_ECUDA, "cudaGetDevice failed");
+  // Device address of g_scratch on the current device (host code cannot use the symbol
+  // itself as a device pointer).  Looked up on every call, with the device current: the
+  // lookup allocates nothing, and a pointer cached across calls would go stale when the
+  // caller resets the device (the module, and with it the array, is loaded anew).
   unsigned char *scratch = nullptr;
   {
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
-      void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess) return reject(SWARM_ECUDA, cudaGetErrorString(e));
-      g_addr[dev] = p;
-    }
-    scratch = static_cast<unsigned char *>(g_addr[dev]);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) return reject(SWARM_ECUDA, e != cudaSuccess ? cudaGetErrorString(e) : "no scratch address");
+    scratch = static_cast<unsigned char *>(p);
   }
 
   swarm::BinView B;
@@ -102,7 +103,8 @@ extern "C" int swarm_hermite_integrate_noalloc(int32_t n, int32_t n_sys, int32_t
   P.work_next = reinterpret_cast<int *>(scratch + 128);
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  noalloc_setup_kernel<<<(int)((units + 255) / 256), 256, 0, st>>>(scratch, B, (int)units, mapping);
+  const long long setup_threads = units > n_sys ? units : n_sys;
+  noalloc_setup_kernel<<<(int)((setup_threads + 255) / 256), 256, 0, st>>>(scratch, B, (int)units, mapping, t_end, dt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return reject(SWARM_ECUDA, cudaGetErrorString(e));
   int sms = 0;

@@ -270,6 +270,10 @@ extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_bo
   if (n_body < SWARM_MIN_N || n_body > SWARM_RING_MAX_N) return sfail(SWARM_EINVAL, "n_body must be in 2..15");
   if (integrator < SWARM_HERMITE4 || integrator > SWARM_MVS_JACOBI) return sfail(SWARM_EINVAL, "unknown integrator");
   if (!std::isfinite(t0) || !std::isfinite(t_end)) return sfail(SWARM_EINVAL, "t0 and t_end must be finite");
+  {
+    const double dt = integrator == SWARM_HERMITE4 ? sv->cfg.hermite_dt : sv->cfg.mvs_dt;
+    if (!(std::fabs(t_end - t0) / dt <= kMaxCallSteps)) return sfail(SWARM_EINVAL, "more than 2e9 steps in one request");
+  }
   if (n_sys > ((sv->cfg.slots_per_pool + 31) / 32 * 32)) return sfail(SWARM_EINVAL, "request larger than a slot pool");
   const size_t nb = (size_t)n_sys * n_body;
   for (size_t i = 0; i < nb; i++)

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libswarm_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 HERMITE4, MVS_DH, MVS_JACOBI, HERMITE4_ADAPTIVE, RKCK, RKCK_ADAPTIVE = 1, 2, 3, 4, 5, 6
-ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE = range(6)
+ACTIVE, DONE, CLOSE_ENCOUNTER, EJECTED, KEPLER_NOCONV, NONFINITE, SPAN_LIMIT = range(7)
 MAP_AUTO, MAP_SYSTEM_PER_LANE, MAP_BODY_PER_LANE, MAP_PLAIN_PER_STEP = range(4)
 OPT_MAPPING, OPT_N_CORR, OPT_LOG_INTERVAL, OPT_LOG_CAPACITY, OPT_STEPS_PER_LAUNCH, OPT_SINGLE_LAUNCH, OPT_CTAS_PER_SM, OPT_CORRECTOR = range(1, 9)
 

@@ -86,3 +86,66 @@ def test_noalloc_rejects_oversized_ensembles():
     rc = f(3, 65521 * 32, 65521 * 32, dummy, dummy, dummy, dummy, dummy, 1.0, 0.1, 0.0, 0.0, None)
     assert rc == -1
     assert b"too large" in S_mod.lib().swarm_last_error()
+
+
+def test_noalloc_unpadded_rows_and_stopped_systems_untouched():
+    """s_pad = n_sys (not a multiple of 32) and a few systems already stopped on entry:
+    the stopped ones keep x, v, t and status bit for bit, the others match the regular
+    entry point given the same statuses."""
+    torch = pytest.importorskip("torch")
+    S_mod, f = _fn()
+    n, S = 4, 45
+    ens = ics.request_ensemble({"n_sys": S, "n": n, "seed": 91})
+    x, v, m, t, st = _to_bin(ens, n, S, torch)
+    stopped = np.zeros(S, np.int32)
+    stopped[::7] = S_mod.CLOSE_ENCOUNTER
+    stopped[3] = S_mod.EJECTED
+    st.copy_(torch.from_numpy(stopped))
+    x0, v0 = x.clone(), v.clone()
+    stream = torch.cuda.current_stream()
+    ref = S_mod.Ensemble(ens, stream=stream)
+    ref.set_stop(3.0, 100.0)
+    ref.set_state(ens["pos"], ens["vel"], time=[0.0] * S, status=stopped)
+    for t_end in (200 * DT, 450 * DT):
+        rc = f(n, S, S, x.data_ptr(), v.data_ptr(), m.data_ptr(), t.data_ptr(), st.data_ptr(), t_end, DT, 3.0, 100.0,
+               stream.cuda_stream)
+        assert rc == 0, S_mod.lib().swarm_last_error()
+        torch.cuda.synchronize()
+        got = _from_bin(x, v, t, st, S, n)
+        ref.integrate(t_end, S_mod.HERMITE4, DT)
+        want = ref.state()
+        assert np.array_equal(got["status"], want["status"])
+        keep = stopped > S_mod.DONE
+        assert np.array_equal(got["status"][keep], stopped[keep])
+        assert np.all(got["time"][keep] == 0.0)
+        assert torch.equal(x[:, :, torch.from_numpy(keep).cuda()], x0[:, :, torch.from_numpy(keep).cuda()])
+        assert torch.equal(v[:, :, torch.from_numpy(keep).cuda()], v0[:, :, torch.from_numpy(keep).cuda()])
+        run = ~keep
+        np.testing.assert_allclose(got["time"][run], want["time"][run], rtol=1e-14, atol=0)
+        ex, ev = per_system_errors(ens, got, want)
+        assert ex.max() <= TOL and ev.max() <= TOL, (ex.max(), ev.max())
+    ref.close()
+
+
+def test_noalloc_marks_spans_beyond_the_step_limit():
+    """A call asking more than 2e9 fixed steps of a system leaves it where it is with
+    status SPAN_LIMIT (the times are on the device, so the check is per system there);
+    already stopped systems keep their status."""
+    torch = pytest.importorskip("torch")
+    S_mod, f = _fn()
+    n, S = 3, 40
+    ens = ics.three_body(S, seed=5)
+    x, v, m, t, st = _to_bin(ens, n, 64, torch)
+    st[5] = S_mod.EJECTED
+    x0, v0 = x.clone(), v.clone()
+    stream = torch.cuda.current_stream()
+    rc = f(n, S, 64, x.data_ptr(), v.data_ptr(), m.data_ptr(), t.data_ptr(), st.data_ptr(), 2.5e9 * DT, DT, 3.0,
+           100.0, stream.cuda_stream)
+    assert rc == 0, S_mod.lib().swarm_last_error()
+    torch.cuda.synchronize()
+    status = st.cpu().numpy()
+    want = np.full(S, S_mod.SPAN_LIMIT, np.int32)
+    want[5] = S_mod.EJECTED
+    assert np.array_equal(status, want)
+    assert torch.equal(x, x0) and torch.equal(v, v0)
+    assert np.all(t.cpu().numpy() == 0.0)
