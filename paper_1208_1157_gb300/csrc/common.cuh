@@ -83,6 +83,22 @@ __device__ __forceinline__ bool nonneg_lt(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
+// 1/d for a positive normal d, to a few ulp: the approximate reciprocal of the hardware
+// (rcp.approx.ftz.f64) refined by one Newton-Raphson step r' = r + r (1 - d r), which
+// squares its relative error.  For Newton corrections, whose own accuracy only has to
+// beat the remaining error of the iteration by a wide margin, not for results.
+__device__ __forceinline__ double rcp_newton(const F64k &k, double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  return fma(r, fma(-d, r, k.one), r);
+}
+
+// |a| < 2^e for a double a, on the exponent bits (integer pipe): true when the biased
+// exponent of a is below that of 2^e (NaN and infinity give false).
+__device__ __forceinline__ bool abs_below_pow2(double a, int e) {
+  return (__double2hiint(a) & 0x7ff00000) < ((1023 + e) << 20);
+}
+
 // Most fixed steps one call may ask of a system (below 2^31, so a step count is exact in
 // an int).  Every entry point rejects longer spans before launching: swarm_integrate and
 // swarm_server_submit on the host, the allocation-free entry point per system on the

@@ -82,7 +82,7 @@ __device__ __forceinline__ void ring_acc(const F64k &k, const double (&x)[3], do
 // z ~ 0.1, so the series alone usually serves.
 __device__ __forceinline__ void stumpff23(double z, double &c2, double &c3) {
   int k = 0;
-  while (fabs(z) > 0.25 && k < 40) {
+  while (!abs_below_pow2(z, -2) && k < 40) {  // |z| >= 0.25, tested on the exponent bits
     z *= 0.25;
     k++;
   }
@@ -127,7 +127,8 @@ __device__ __forceinline__ KepConst kep_const(double mu) {
 }
 
 // Starting guesses of Vallado, "Fundamentals of Astrodynamics and Applications",
-// Algorithm 8 (elliptic, hyperbolic, parabolic).
+// Algorithm 8 (elliptic, hyperbolic, parabolic): for drifts longer than about a radian of
+// eccentric anomaly, where the Taylor start below does not hold.
 static __device__ __noinline__ double chi_guess(const KepConst &K, const double (&r)[3], const double (&v)[3], double r0, double sig0,
                             double alpha, double h) {
   if (alpha > 1e-6) return K.smu * alpha * h;
@@ -144,107 +145,135 @@ static __device__ __noinline__ double chi_guess(const KepConst &K, const double 
   return sqrt(p) * 2.0 / tan(2.0 * w);
 }
 
-// Universal-variable Kepler drift of (r, v) by h: Newton on
-//   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
-// Starting point of the next Kepler solve of a planet: its last three solutions, which
-// (steps of equal length) extrapolate quadratically to within the orbit's third
-// difference (linearly from two, the last one alone after the first step).
-struct ChiState {
-  double chi = 0.0, prev = 0.0, prev2 = 0.0;
-  int n = 0;  // solutions held (0..3)
-};
-
-// Universal-variable Kepler drift of (r, v) by h: Newton on
-//   F(chi) = (r0.v0/sqrt mu) chi^2 c2 + (1 - alpha r0) chi^3 c3 + r0 chi - sqrt(mu) h,
-// F'(chi) = |r(chi)|, until |d chi| <= 1e-14 max(1, |chi|), or until the error left after
-// the step, which for Newton is (F''/2F') d chi^2 with F'' = s0 (1 - z c2) + beta chi
-// (1 - z c3), is below 1e-16 |chi| (half an ulp of chi: the root to rounding, the one the
-// oracle's first test alone reaches, usually one iteration sooner); then the Lagrange f,
-// g, fdot, gdot.  `cs` carries the previous solutions as the starting point (none on the
-// first step of a call: Vallado's guess).  Executed by every lane of the warp; lanes with
-// `on` false do not change their state.  Returns false on non-convergence in 50
-// iterations.
+// Universal-variable Kepler drift of (r, v) by h.  The universal anomaly chi solves
+//   F(chi) = s0 U2 + beta U3 + r0 chi - sqrt(mu) h = 0,   U_k = chi^k c_k(alpha chi^2),
+// s0 = r0.v0/sqrt(mu), beta = 1 - alpha r0, with F' = |r(chi)|, F'' = s0 U0 + beta U1 and
+// F''' = beta U0 - alpha s0 U1 (U3' = U2, U2' = U1, U1' = U0, U0' = -alpha U1).
+//  - Start: the Taylor series of chi(t) about the current state to fourth order in h,
+//    from d chi/dt = sqrt(mu)/r, dr/dt = sigma/r, d sigma/dt = v^2 - mu/r and
+//    d v^2/dt = -2 mu sigma/r^3 (sigma = r.v, u = 1/r); the derivatives are
+//      1st: sqrt(mu) u,  2nd: -sqrt(mu) sigma u^3,
+//      3rd: -sqrt(mu) u^3 (v^2 - mu u - 3 sigma^2 u^2),
+//      4th: sqrt(mu) sigma u^5 (9 v^2 - 8 mu u - 15 sigma^2 u^2).
+//    Its error is of order e (n h)^5/120 of chi for eccentricity e and mean motion n
+//    (~4e-7 relative for e = 0.1 and steps of 1/20 orbit).  Beyond about a radian of
+//    eccentric anomaly (|alpha| (sqrt(mu) u h)^2 >= 1) Vallado's guesses are taken instead.
+//  - First iteration: Halley's method, cubic convergence, its remaining error
+//    |F'''/(6F') - (F''/(2F'))^2| dchi^3; later iterations (rare) Newton's, remaining
+//    error |F''/(2F')| dchi^2.  Stop when that error is below 1e-16 |chi| (half an ulp: the
+//    root to rounding) or |dchi| <= 1e-14 max(1, |chi|) (the oracle's test).  One Halley
+//    step from the Taylor start meets the first test for moderate eccentricities.
+//  - The universal functions at the root come from those of the last iterate by a
+//    third-order Taylor step in its correction (exact to rounding for |dchi| <= 1e-5
+//    max(1, |chi|), dropped terms ~ dchi^4/24; else recomputed at the root); then the
+//    Lagrange f, g, fdot, gdot.
+// Executed by every lane of the warp; lanes with `on` false do not change their state.
+// Returns false on non-convergence in 50 iterations.  The corrections divide by
+// rcp_newton, whose error (~1e-13 relative at most) only scales the small last correction.
 // RQ: rq holds 1/|r| of the current r on entry (computed by the same expression); on exit
 // the lanes that drifted hold 1/|r| of the new r there.
 template <bool RQ>
-static __device__ __noinline__ bool kepler_drift(const F64k k, bool on, const KepConst &K, double (&r)[3], double (&v)[3],
-                                                 double h, ChiState &cs, int &iters, double &rq) {
+__device__ __forceinline__ bool kepler_drift(const F64k k, bool on, const KepConst &K, double (&r)[3], double (&v)[3],
+                                             double h, int &iters, double &rq) {
   const double r2 = fma(r[2], r[2], fma(r[1], r[1], kmul(k, r[0], r[0])));
-  const double rinv0 = RQ ? rq : rsqrt(r2);
-  const double r0 = kmul(k, r2, rinv0);
+  const double u = RQ ? rq : rsqrt(r2);  // 1/r0
+  const double r0 = kmul(k, r2, u);
   const double sig0 = fma(r[2], v[2], fma(r[1], v[1], kmul(k, r[0], v[0])));
   const double v2 = fma(v[2], v[2], fma(v[1], v[1], kmul(k, v[0], v[0])));
-  const double alpha = fma(-v2, K.muinv, kmul(k, 2.0, rinv0));
+  const double mu_u = kmul(k, K.mu, u);
+  const double alpha = kmul(k, ksub(k, kmul(k, 2.0, mu_u), v2), K.muinv);  // (2 mu/r0 - v^2)/mu
   const double s0 = kmul(k, sig0, K.smuinv);
   const double beta = fma(-alpha, r0, 1.0);
   const double target = kmul(k, K.smu, h);
-  double x = cs.n >= 3 ? fma(3.0, ksub(k, cs.chi, cs.prev), cs.prev2) : cs.n == 2 ? 2.0 * cs.chi - cs.prev : cs.chi;
-  if (on && cs.n == 0) x = chi_guess(K, r, v, r0, sig0, alpha, h);
+  const double ms0a = kmul(k, -alpha, s0);
+  // fourth-order Taylor start: chi = h (T1 + h (T2 + h (T3 + h T4)))
+  const double T1 = kmul(k, K.smu, u);  // sqrt(mu) u
+  const double su = kmul(k, sig0, u);   // sigma u
+  const double su2 = kmul(k, su, su);
+  const double Pu = kmul(k, T1, u);     // sqrt(mu) u^2
+  const double Q = kmul(k, Pu, u);      // sqrt(mu) u^3
+  const double A = ksub(k, v2, mu_u);   // v^2 - mu u
+  const double T2 = kmul(k, kmul(k, -0.5, Pu), su);
+  const double T3 = kmul(k, kmul(k, Q, -1.0 / 6.0), fma(-3.0, su2, A));
+  const double T4 = kmul(k, kmul(k, kmul(k, Q, su), 1.0 / 24.0), fma(-15.0, su2, fma(9.0, A, mu_u)));
+  double x = kmul(k, h, fma(h, fma(h, fma(h, T4, T3), T2), T1));
+  const double x1 = kmul(k, T1, h);
+  if (on && !abs_below_pow2(kmul(k, alpha, kmul(k, x1, x1)), 0)) x = chi_guess(K, r, v, r0, sig0, alpha, h);
   bool done = !on;
   int it = 0;
-  // universal functions U0..U3 (U_k = chi^k c_k(alpha chi^2)) at the last iterate and its
-  // Newton correction: with U3' = U2, U2' = U1, U1' = U0, U0' = -alpha U1 they move to the
-  // root by a second-order Taylor step, which is exact to rounding for the small final
-  // corrections (|d chi| <= 1e-6 max(1, |chi|), dropped terms ~ d chi^3)
+  // universal functions U0..U3 at the last iterate and its correction dx
   double U0 = 1.0, U1 = 0.0, U2 = 0.0, U3 = 0.0, dx = 0.0;
   for (int i = 0; i < 50; i++) {
     if (__all_sync(0xffffffffu, done)) break;
     if (!done) {
-      const double x2 = kmul(k, x, x);
-      const double z = kmul(k, alpha, x2);
+      const double xx = kmul(k, x, x);
+      const double z = kmul(k, alpha, xx);
       double c2, c3;
       stumpff23(z, c2, c3);
       U0 = fma(-z, c2, 1.0);
       U1 = kmul(k, x, fma(-z, c3, 1.0));
-      U2 = kmul(k, x2, c2);
-      U3 = kmul(k, kmul(k, x2, x), c3);
+      U2 = kmul(k, xx, c2);
+      U3 = kmul(k, kmul(k, xx, x), c3);
       const double F = fma(s0, U2, fma(beta, U3, fma(r0, x, -target)));
       const double dF = fma(s0, U1, fma(beta, U2, r0));  // |r(chi)|
       const double ddF = fma(s0, U0, kmul(k, beta, U1));
-      dx = F / dF;
+      double err;
+      if (it == 0) {  // Halley
+        const double D = fma(kmul(k, -0.5, F), ddF, kmul(k, dF, dF));
+        const double rD = rcp_newton(k, D);
+        const double idF = kmul(k, dF, rD);  // ~1/F' (D = F'^2 (1 + O(F)))
+        dx = kmul(k, kmul(k, F, dF), rD);
+        const double dddF = fma(ms0a, U1, kmul(k, beta, U0));
+        const double g2 = kmul(k, kmul(k, 0.5, ddF), idF);
+        const double C = fma(-g2, g2, kmul(k, kmul(k, dddF, idF), 1.0 / 6.0));
+        err = kmul(k, kmul(k, fabs(C), fabs(dx)), kmul(k, dx, dx));
+      } else {  // Newton
+        const double idF = rcp_newton(k, dF);
+        dx = kmul(k, F, idF);
+        err = kmul(k, kmul(k, kmul(k, 0.5, fabs(ddF)), idF), kmul(k, dx, dx));
+      }
       x = ksub(k, x, dx);
       it++;
-      if (fabs(dx) <= kmul(k, 1e-14, fmax(1.0, fabs(x))) ||
-          kmul(k, fabs(ddF), kmul(k, dx, dx)) <= kmul(k, kmul(k, 2e-16, fabs(x)), fabs(dF)))
+      const double adx = fabs(dx), ax = fabs(x);
+      if (nonneg_lt(err, kmul(k, 1e-16, ax)) || !nonneg_lt(1e-14, adx) || !nonneg_lt(kmul(k, 1e-14, ax), adx))
         done = true;
     }
   }
   iters = it;
   if (!on) return true;
   if (!done) return false;
-  if (fabs(dx) <= 1e-6 * fmax(1.0, fabs(x))) {
-    const double d2h = kmul(k, kmul(k, 0.5, dx), dx);
-    const double U1n = fma(kmul(k, -alpha, U1), d2h, fma(-U0, dx, U1));
-    const double U2n = fma(U0, d2h, fma(-U1, dx, U2));
-    U3 = fma(U1, d2h, fma(-U2, dx, U3));
-    U1 = U1n;
+  const double d = -dx;  // last iterate -> root
+  if (nonneg_lt(fabs(d), 1e-5) || nonneg_lt(fabs(d), kmul(k, 1e-5, fabs(x)))) {
+    const double d2 = kmul(k, kmul(k, 0.5, d), d);        // d^2/2
+    const double d3 = kmul(k, kmul(k, d2, d), 1.0 / 3.0);  // d^3/6
+    const double aU1 = kmul(k, alpha, U1), aU0 = kmul(k, alpha, U0);
+    const double U3n = fma(U0, d3, fma(U1, d2, fma(U2, d, U3)));
+    const double U2n = fma(-aU1, d3, fma(U0, d2, fma(U1, d, U2)));
+    U1 = fma(-aU0, d3, fma(-aU1, d2, fma(U0, d, U1)));
     U2 = U2n;
+    U3 = U3n;
   } else {  // a large last correction: evaluate at the root
-    const double x2 = x * x;
-    const double z = alpha * x2;
+    const double xx = x * x;
+    const double z = alpha * xx;
     double c2, c3;
     stumpff23(z, c2, c3);
     U1 = x * fma(-z, c3, 1.0);
-    U2 = x2 * c2;
-    U3 = x2 * x * c3;
+    U2 = xx * c2;
+    U3 = xx * x * c3;
   }
-  const double f = fma(-U2, rinv0, 1.0);
+  const double f = fma(-U2, u, 1.0);
   const double g = fma(-U3, K.smuinv, h);
   double rn[3];
 #pragma unroll
   for (int c = 0; c < 3; c++) rn[c] = fma(f, r[c], kmul(k, g, v[c]));
   const double rinv = rsqrt(fma(rn[2], rn[2], fma(rn[1], rn[1], kmul(k, rn[0], rn[0]))));
-  const double fd = kmul(k, kmul(k, -K.smu, U1), kmul(k, rinv0, rinv));
+  const double fd = kmul(k, kmul(k, -K.smu, U1), kmul(k, u, rinv));
   const double gd = fma(-U2, rinv, 1.0);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     v[c] = fma(fd, r[c], kmul(k, gd, v[c]));
     r[c] = rn[c];
   }
-  cs.prev2 = cs.prev;
-  cs.prev = cs.chi;
-  cs.chi = x;
-  cs.n = cs.n < 3 ? cs.n + 1 : 3;
   rq = rinv;
   return true;
 }
@@ -433,7 +462,6 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
 
   bool alive = runnable;
   int steps_done = 0;
-  ChiState cs;
   unsigned long long kep_iters = 0;
 
   for (int k = 1; k <= Nmax; k++) {
@@ -459,7 +487,7 @@ __device__ __forceinline__ void bpl_mvs_body(const BinView &B, const StepParams 
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     // Keplerian drift of every planet
     int its = 0;
-    bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, cs, its, rq);
+    bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, its, rq);
     kep_iters += its;
     // accelerations at the new positions, reused by the next step's first kick
     mvs_acc<N, JAC, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2, rq);
@@ -613,7 +641,6 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
   int kg = 0;
   double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
   double rq = 1.0;  // Jacobi: 1/|q| of the current q (planets)
-  ChiState cs;
   unsigned long long kep_iters = 0;
 #pragma unroll
   for (int r = 0; r < RTA; r++) kc[r] = 0.0;
@@ -681,7 +708,6 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
           u[c] = un[c];
           acc[c] = an[c];
         }
-        cs = ChiState();
         has = plan.N > 0;
         if (runnable && plan.N == 0 && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
       }
@@ -708,7 +734,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
 #pragma unroll
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
-    const bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, cs, its, rq);
+    const bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, its, rq);
     kep_iters += its;
     double Q[3], d2[RTA];
 #pragma unroll

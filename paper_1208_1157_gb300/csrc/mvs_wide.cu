@@ -202,7 +202,6 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
   double q[3], u[3], acc[3], Q[3];
   wide_to_canonical<JAC>(x, v, W, b, real, lane, q, u);
   wide_mvs_acc<JAC>(P.fk, q, W, b, n, real, lane, acc, Q, d2s);
-  ChiState cs;
   unsigned long long kep_iters = 0;
   int steps = 0, code = 0;
   for (int k = 1; k <= plan.N; k++) {
@@ -223,7 +222,7 @@ __device__ __forceinline__ void wide_mvs_body(const BinView &B, const StepParams
     for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
     int its = 0;
     double rqw = 1.0;
-    const bool ok = kepler_drift<false>(P.fk, real && b != 0, K, q, u, h, cs, its, rqw);
+    const bool ok = kepler_drift<false>(P.fk, real && b != 0, K, q, u, h, its, rqw);
     kep_iters += its;
     wide_mvs_acc<JAC>(P.fk, q, W, b, n, real, lane, acc, Q, d2s);
 #pragma unroll

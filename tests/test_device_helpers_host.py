@@ -19,12 +19,39 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
                    "mvs_impl.cuh")
 
 
+HOST_SHIMS = (
+    "#include <cmath>\n#include <cstdio>\n#include <cstdlib>\n#include <cstring>\n"
+    "using std::fabs; using std::fma; using std::sqrt; using std::fmax;\n"
+    "#define __device__\n#define __forceinline__ inline\n#define __noinline__\n"
+    "static inline int __double2hiint(double a) { long long b; std::memcpy(&b, &a, 8); return (int)(b >> 32); }\n"
+    "static inline long long __double_as_longlong(double a) { long long b; std::memcpy(&b, &a, 8); return b; }\n"
+    "static inline bool __all_sync(unsigned, bool p) { return p; }\n"
+    "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n")
+
+
+def common_helpers():
+    """The scalar helpers of csrc/common.cuh the Kepler drift and the Stumpff functions use
+    (F64k forms, integer-pipe compares, the refined reciprocal), as host code; the
+    reciprocal's hardware seed (inline PTX) becomes an exact 1/d."""
+    common = open(COMMON).read()
+    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
+                     common, re.S).group(0)
+    out = [f64k]
+    for sig in (r"bool nonneg_lt\(double a, double b\)", r"bool abs_below_pow2\(double a, int e\)",
+                r"double rcp_newton\(const F64k &k, double d\)"):
+        out.append(re.search(r"__device__ __forceinline__ " + sig + r" \{.*?\n\}\n", common, re.S).group(0))
+    text = "".join(out)
+    seed = re.search(r'  asm\("rcp\.approx\.ftz\.f64 %0, %1;" : "=d"\(r\) : "d"\(d\)\);\n', text)
+    assert seed, "the reciprocal seed is not in common.cuh"
+    return text.replace(seed.group(0), "  r = 1.0 / d;\n")
+
+
 def build_stumpff(d):
     """Host build of the kernel's stumpff23 (from SRC) in directory d."""
     text = open(SRC).read()
     fn = re.search(r"__device__ __forceinline__ void stumpff23\(double z, double &c2, double &c3\) \{.*?\n\}\n",
-                   text, re.S).group(0).replace("__device__ __forceinline__ ", "static ")
-    prog = ("#include <cmath>\n#include <cstdio>\n#include <cstdlib>\nusing std::fabs; using std::fma;\n" + fn +
+                   text, re.S).group(0)
+    prog = (HOST_SHIMS + "namespace swarm {\n" + common_helpers() + fn + "}\nusing swarm::stumpff23;\n" +
             "int main(int argc, char **argv) {\n"
             "  double z;\n"
             "  while (scanf(\"%lf\", &z) == 1) { double c2, c3; stumpff23(z, c2, c3); printf(\"%.17g %.17g\\n\", c2, c3); }\n"
@@ -141,11 +168,10 @@ int main() {
   const swarm::F64k k = {0.0, -1.0, 1.0};
   while (scanf("%lf %lf %d %lf %lf %lf %lf %lf %lf", &mu, &h, &steps, &r[0], &r[1], &r[2], &v[0], &v[1], &v[2]) == 9) {
     const swarm::KepConst K = swarm::kep_const(mu);
-    swarm::ChiState cs;
     double rq = 1.0;
     for (int s = 0; s < steps; s++) {
       int it = 0;
-      const bool ok = swarm::kepler_drift<false>(k, true, K, r, v, h, cs, it, rq);
+      const bool ok = swarm::kepler_drift<false>(k, true, K, r, v, h, it, rq);
       printf("%d %d %.17g %.17g %.17g %.17g %.17g %.17g\n", ok ? 1 : 0, it, r[0], r[1], r[2], v[0], v[1], v[2]);
     }
   }
@@ -156,18 +182,11 @@ int main() {
 
 def build_kepler(d):
     """Host build of the kernel's kepler_drift (from COMMON and SRC) in directory d."""
-    common = open(COMMON).read()
     mvs = open(SRC).read()
-    f64k = re.search(r"struct F64k \{.*?kadd\(const F64k &k, double a, double b\) \{ return fma\(a, k.one, b\); \}\n",
-                     common, re.S).group(0)
     stumpff = re.search(r"__device__ __forceinline__ void stumpff23\(double z, double &c2, double &c3\) \{.*?\n\}\n",
                         mvs, re.S).group(0)
     kep = mvs[mvs.index("struct KepConst {"):mvs.index("// ---------------------------------------------------------------- coordinate maps")]
-    prog = ("#include <cmath>\n#include <cstdio>\nusing std::fabs; using std::fma; using std::sqrt; using std::fmax;\n"
-            "#define __device__\n#define __forceinline__ inline\n#define __noinline__\n"
-            "static inline bool __all_sync(unsigned, bool p) { return p; }\n"
-            "static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }\n"
-            "namespace swarm {\n" + f64k + stumpff + kep + "}\n" + KEPLER_MAIN)
+    prog = HOST_SHIMS + "namespace swarm {\n" + common_helpers() + stumpff + kep + "}\n" + KEPLER_MAIN
     with open(os.path.join(d, "k.cpp"), "w") as f:
         f.write(prog)
     exe = os.path.join(d, "k")
@@ -227,9 +246,9 @@ def drift_run(exe, mu, h, steps, r, v):
 
 
 def check_kepler_elliptic(kepler_exe, e):
-    # the kernel's drift (extrapolated start, quadratic stop, Taylor finalize) over 60 steps
-    # of 1/20 orbit against Kepler's equation: the state to 1e-13, two or three Newton
-    # iterations per step once the extrapolation has three solutions
+    # the kernel's drift (fourth-order Taylor start, one Halley step, error-bound stop,
+    # Taylor finalize) over 60 steps of 1/20 orbit against Kepler's equation: the state to
+    # 1e-13; a single iteration per step for e <= 0.05, at most two for e <= 0.3
     mu, a = 1.0 + 1e-3, 1.3
     r0 = [a * (1 - e), 0.0, 0.01]
     v0 = [0.0, float(np.sqrt(mu * (1 + e) / (a * (1 - e)))), 0.002]
@@ -241,8 +260,10 @@ def check_kepler_elliptic(kepler_exe, e):
         rx, vx = kepler_exact(mu, r0, v0, h * (s + 1))
         assert np.max(np.abs(rows[s, 2:5] - rx)) <= 1e-13 * np.max(np.abs(rx)) * (s + 1)
         assert np.max(np.abs(rows[s, 5:8] - vx)) <= 1e-13 * np.max(np.abs(vx)) * (s + 1)
+    if e <= 0.05:
+        assert np.all(rows[:, 1] == 1), rows[:, 1]
     if e <= 0.3:
-        assert rows[3:, 1].max() <= 3
+        assert rows[:, 1].max() <= 2, rows[:, 1]
 
 
 @pytest.mark.parametrize("e", [0.0, 0.05, 0.3, 0.9])
@@ -517,10 +538,12 @@ KERNEL_MUTANTS = [
     ("error_weight", "rkck_impl.cuh", "E5 = 277.0 / 114688.0", "E5 = 277.0 / 114689.0", "constants"),
     ("stumpff_term", "mvs_impl.cuh", "c2 = fma(z, c2, 1.0 / 40320.0);", "c2 = fma(z, c2, 1.0 / 40321.0);", "series"),
     ("stumpff_doubling", "mvs_impl.cuh", "c3 = 0.25 * fma(c0, c3, c2);", "c3 = 0.5 * fma(c0, c3, c2);", "doubling"),
-    ("kepler_taylor_sign", "mvs_impl.cuh", "const double U2n = fma(U0, d2h, fma(-U1, dx, U2));",
-     "const double U2n = fma(U0, d2h, fma(U1, dx, U2));", "kepler"),
-    ("kepler_fdot_sign", "mvs_impl.cuh", "kmul(k, kmul(k, -K.smu, U1), kmul(k, rinv0, rinv))",
-     "kmul(k, kmul(k, K.smu, U1), kmul(k, rinv0, rinv))", "kepler"),
+    ("kepler_taylor_sign", "mvs_impl.cuh", "const double U2n = fma(-aU1, d3, fma(U0, d2, fma(U1, d, U2)));",
+     "const double U2n = fma(-aU1, d3, fma(U0, d2, fma(-U1, d, U2)));", "kepler"),
+    ("kepler_start_sign", "mvs_impl.cuh", "const double T2 = kmul(k, kmul(k, -0.5, Pu), su);",
+     "const double T2 = kmul(k, kmul(k, 0.5, Pu), su);", "kepler"),
+    ("kepler_fdot_sign", "mvs_impl.cuh", "kmul(k, kmul(k, -K.smu, U1), kmul(k, u, rinv))",
+     "kmul(k, kmul(k, K.smu, U1), kmul(k, u, rinv))", "kepler"),
     ("relative_indirect_sign", "hermite.cuh", "A[k][c] = fma(-m0s[k], X[k][c], -IA[c]);",
      "A[k][c] = fma(-m0s[k], X[k][c], IA[c]);", "relative"),
     ("series_refinement_sign", "hermite.cuh", "fma(0.375, del[i][k], -0.5)", "fma(0.375, del[i][k], 0.5)", "relative"),
