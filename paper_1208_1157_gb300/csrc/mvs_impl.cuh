@@ -74,6 +74,60 @@ __device__ __forceinline__ void ring_acc(const F64k &k, const double (&x)[3], do
   }
 }
 
+// The same acceleration with the rounds spread over R copies of the system (spread mode:
+// groups g0 .. g0 + R - 1 of NG lanes each hold a copy, group g0 + rho being replica rho).
+// Replica rho evaluates the rounds r with (r - 1) % R == rho; then every lane
+// gathers each round's terms from the replica that evaluated it and accumulates them in
+// round order with the FMAs of ring_acc, so the result is bit for bit that of ring_acc.
+template <int M, int OFF, int NG, int R>
+__device__ __forceinline__ void ring_acc_rep(const F64k &k, const double (&x)[3], double m, int j, int base, int rho,
+                                             int g0, double (&a)[3], double (&d2)[ARing<M>::RTA]) {
+  constexpr int RF = ARing<M>::RF, RT = ARing<M>::RT;
+  constexpr int NS = (RT + R - 1) / R;  // rounds per replica
+  double dxs[NS][3], sps[NS], sis[NS], r2s[NS];
+#pragma unroll
+  for (int sl = 0; sl < NS; sl++) {
+    const int r = rho + 1 + sl * R;  // this replica's sl-th round (past RT: unused)
+    int p = j + r;
+    while (p >= M) p -= M;
+#pragma unroll
+    for (int c = 0; c < 3; c++) dxs[sl][c] = ksub(k, shfl(x[c], base + OFF + p), x[c]);
+    const double mp = shfl(m, base + OFF + p);
+    double r2 = kmul(k, dxs[sl][0], dxs[sl][0]);
+    r2 = fma(dxs[sl][1], dxs[sl][1], r2);
+    r2 = fma(dxs[sl][2], dxs[sl][2], r2);
+    const double rh = rsqrt(r2);
+    const double rho3 = kmul(k, kmul(k, rh, rh), rh);
+    sps[sl] = kmul(k, mp, rho3);
+    sis[sl] = kmul(k, m, rho3);
+    r2s[sl] = r2;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) a[c] = 0.0;
+#pragma unroll
+  for (int r = 1; r <= RT; r++) {
+    const int sl = (r - 1) / R;
+    const int src = (g0 + (r - 1) % R) * NG + OFF;  // member 0 of the evaluating replica
+    double dx[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) dx[c] = shfl(dxs[sl][c], src + j);
+    const double sp = shfl(sps[sl], src + j);
+#pragma unroll
+    for (int c = 0; c < 3; c++) a[c] = fma(sp, dx[c], a[c]);
+    if (r <= RF) {  // full round: the share of the pair (j - r, j) evaluated by member j - r
+      int q = j - r;
+      if (q < 0) q += M;
+      double rdx[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) rdx[c] = shfl(dxs[sl][c], src + q);
+      const double rs = shfl(sis[sl], src + q);
+#pragma unroll
+      for (int c = 0; c < 3; c++) a[c] = fma(-rs, rdx[c], a[c]);
+    }
+    d2[r - 1] = shfl(r2s[sl], src + j);
+  }
+}
+
 // ---------------------------------------------------------------- Stumpff and Kepler
 // c2(z), c3(z) by their power series (8 terms each; on |z| <= 0.25 within 2.3e-16
 // relative of the closed forms), reaching larger |z| by quartering the argument and the
@@ -354,12 +408,16 @@ __device__ __forceinline__ void jacobi_helio(const F64k &k, const double (&q)[3]
 // Interaction acceleration.  DH: planet-planet terms (Sec. 2.2.3).  Jacobi: Jacobi
 // components of all pair accelerations plus mu_b r'_b/|r'_b|^3.
 // RQ (Jacobi): rq holds 1/|q| on entry; otherwise it is computed and stored there.
-template <int N, bool JAC, bool RQ = false>
+// R > 1: the spread mode, the ring's rounds shared out over R replicas starting at group
+// g0 (ring_acc_rep).
+template <int N, bool JAC, bool RQ = false, int R = 1>
 __device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], double m, double w, double eta_prev_inv, double mu,
                                         int b, int base, double (&acc)[3], double (&Q)[3],
-                                        double (&d2)[ARing<(JAC ? N : N - 1)>::RTA], double &rq) {
+                                        double (&d2)[ARing<(JAC ? N : N - 1)>::RTA], double &rq, int rho = 0,
+                                        int g0 = 0) {
   if constexpr (!JAC) {
-    ring_acc<N - 1, 1>(fk, q, m, b == 0 ? 0 : b - 1, base, acc, d2);
+    if constexpr (R == 1) ring_acc<N - 1, 1>(fk, q, m, b == 0 ? 0 : b - 1, base, acc, d2);
+    else ring_acc_rep<N - 1, 1, N, R>(fk, q, m, b == 0 ? 0 : b - 1, base, rho, g0, acc, d2);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       if (b == 0) acc[c] = 0.0;
@@ -368,7 +426,8 @@ __device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], do
   } else {
     jacobi_helio<N>(fk, q, w, b, Q);
     double a[3];
-    ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
+    if constexpr (R == 1) ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
+    else ring_acc_rep<N, 0, N, R>(fk, Q, m, b, base, rho, g0, a, d2);
     double rho;
     if (RQ) {
       rho = rq;
@@ -606,13 +665,209 @@ __device__ __noinline__ void bpl_mvs_unit(const BinView &B, const StepParams &P,
 // costs the warp one round (the new systems' coordinate maps and first force
 // evaluation) during which the other groups wait.  Per system the arithmetic is that of
 // bpl_mvs_body, step for step.
+//
+// Spread mode.  Once the bin's list is exhausted and A <= G/2 groups of a warp still hold
+// systems, their step latency is all that is left for the warp (with one warp per
+// sub-partition, each FP64 instruction costs its 64 cycles whatever the number of active
+// lanes).  Each system is then copied into R = min(G/A, ring rounds) groups, and the
+// acceleration ring's rounds and the monitor's pair tests are shared out over the copies
+// (ring_acc_rep: the same bits as one group alone), which shortens the step's FP64 chain;
+// when one of them finishes the rest are laid out again.
+
+// per-lane state of the group's current system (group-uniform except the body's own values)
+template <int RTA>
+struct MvsLane {
+  int s = 0;
+  bool has = false;
+  double m = 1.0, m0 = 1.0, Minv = 1.0, eta_prev_inv = 0.0, w = 1.0, mu = 1.0, m0inv = 1.0;
+  KepConst K;
+  double kc[RTA];
+  LaunchPlan plan;
+  double t0 = 0.0;
+  int kg = 0;
+  double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
+  double rq = 1.0;  // Jacobi: 1/|q| of the current q (planets)
+};
+
+// copy every field of the state of lane `src` (the same body of another group)
+template <int RTA>
+__device__ __forceinline__ void mvs_lane_copy(MvsLane<RTA> &L, int src) {
+  L.s = shfl_i(L.s, src);
+  L.has = shfl_i(L.has ? 1 : 0, src) != 0;
+  L.m = shfl(L.m, src);
+  L.m0 = shfl(L.m0, src);
+  L.Minv = shfl(L.Minv, src);
+  L.eta_prev_inv = shfl(L.eta_prev_inv, src);
+  L.w = shfl(L.w, src);
+  L.mu = shfl(L.mu, src);
+  L.m0inv = shfl(L.m0inv, src);
+  L.K.mu = shfl(L.K.mu, src);
+  L.K.smu = shfl(L.K.smu, src);
+  L.K.smuinv = shfl(L.K.smuinv, src);
+  L.K.muinv = shfl(L.K.muinv, src);
+#pragma unroll
+  for (int r = 0; r < RTA; r++) L.kc[r] = shfl(L.kc[r], src);
+  L.plan.N = shfl_i(L.plan.N, src);
+  L.plan.full = shfl_i(L.plan.full, src);
+  L.plan.exact = shfl_i(L.plan.exact, src);
+  L.plan.h_last = shfl(L.plan.h_last, src);
+  L.plan.t_end = shfl(L.plan.t_end, src);
+  L.t0 = shfl(L.t0, src);
+  L.kg = shfl_i(L.kg, src);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    L.q[c] = shfl(L.q[c], src);
+    L.u[c] = shfl(L.u[c], src);
+    L.acc[c] = shfl(L.acc[c], src);
+  }
+  L.rq = shfl(L.rq, src);
+}
+
+// One step of every group holding a system (R = 1), or of the systems held by R groups
+// each (R > 1: replica rho of the set starting at group g0, whose lanes are gm); on a
+// finish or log point the results are written by the lanes with `writer` set.  Returns
+// whether the lane's system finished.
+template <int N, bool JAC, int R>
+__device__ __forceinline__ bool mvs_stream_step(const BinView &B, const StepParams &P, MvsLane<ARing<(JAC ? N : N - 1)>::RTA> &L,
+                                                int b, int base, int rho, int g0, unsigned gm, bool writer,
+                                                unsigned long long &kep_iters) {
+  constexpr int MR = JAC ? N : N - 1;
+  constexpr int RTA = ARing<MR>::RTA;
+  constexpr unsigned long long NP = JAC ? (unsigned long long)N * (N - 1) / 2 : (unsigned long long)(N - 1) * (N - 2) / 2;
+  const unsigned FULL = 0xffffffffu;
+  const int SP = B.S_pad;
+  const bool active = L.has;
+  if (active) L.kg++;
+  const double h = (active && L.kg == L.plan.N && !L.plan.exact) ? L.plan.h_last : P.dt;
+  const double hh = 0.5 * h;
+  if (!JAC) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, L.u[c]), b, base);
+      L.q[c] = b == 0 ? fma(hh, L.u[c], L.q[c]) : fma(kmul(P.fk, hh, L.m0inv), ps, L.q[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      if (b == 0) L.q[c] = fma(h, L.u[c], L.q[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) L.u[c] = fma(hh, L.acc[c], L.u[c]);
+  int its = 0;
+  const bool ok = kepler_drift<JAC>(P.fk, active && b != 0, L.K, L.q, L.u, h, its, L.rq);
+  if (writer) kep_iters += its;
+  double Q[3], d2[RTA];
+#pragma unroll
+  for (int r = 0; r < RTA; r++) d2[r] = 0.0;
+  mvs_acc<N, JAC, JAC, R>(P.fk, L.q, L.m, L.w, L.eta_prev_inv, L.mu, b, base, L.acc, Q, d2, L.rq, rho, g0);
+#pragma unroll
+  for (int c = 0; c < 3; c++) L.u[c] = fma(hh, L.acc[c], L.u[c]);
+  if (!JAC) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, L.u[c]), b, base);
+      L.q[c] = b == 0 ? fma(hh, L.u[c], L.q[c]) : fma(kmul(P.fk, hh, L.m0inv), ps, L.q[c]);
+      Q[c] = L.q[c];
+    }
+  }
+  // monitor on the heliocentric positions at the end of the step (R > 1: each replica
+  // tests its own rounds' pairs, the ballot over all replicas collects them)
+  const double q2 = fma(Q[2], Q[2], fma(Q[1], Q[1], kmul(P.fk, Q[0], Q[0])));
+  const bool nf = nonfinite(L.q[0]) | nonfinite(L.q[1]) | nonfinite(L.q[2]) | nonfinite(L.u[0]) | nonfinite(L.u[1]) |
+                  nonfinite(L.u[2]);
+  const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
+  bool ce = false;
+  {
+    const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
+#pragma unroll
+    for (int r = 1; r <= RTA; r++) {
+      int p = jm + r;
+      if (p >= MR) p -= MR;
+      double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
+      if ((R == 1 || (r - 1) % R == rho) && L.kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], L.kc[r - 1], q2, q2p))
+        ce = true;
+    }
+  }
+  const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
+  const unsigned bkn = __ballot_sync(FULL, active && !ok) & gm;
+  const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
+  const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
+  const int code = bkn ? SWARM_SYS_KEPLER_NOCONV
+                       : bnf ? SWARM_SYS_NONFINITE
+                             : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
+  const bool finish = active && (code != 0 || L.kg == L.plan.N);
+  const bool want_log = active && !code && P.log_interval > 0 && (L.kg % P.log_interval) == 0;
+  if (__any_sync(FULL, finish || want_log)) {
+    double xo[3], vo[3];
+    if (JAC) from_jacobi<N>(L.q, L.u, L.w, b, base, xo, vo);
+    else from_dh<N>(L.q, L.u, L.m, L.m0, L.Minv, b, base, xo, vo);
+    const double tk = step_time(L.plan, L.kg, L.t0, P.dt);
+    if (__any_sync(FULL, want_log)) {  // the energy sum is a warp collective
+      double e[4];
+      ring_energy<N>(xo, vo, L.m, b, base, e);
+      if (want_log && writer && b == 0) write_log(P, B.gidx[L.s], tk, e);
+    }
+    if (finish && writer) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        B.x[(size_t)(c * N + b) * SP + L.s] = xo[c];
+        B.v[(size_t)(c * N + b) * SP + L.s] = vo[c];
+      }
+      if (b == 0) {
+        B.t[L.s] = tk;
+        B.status[L.s] = code ? code : (L.plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
+        if (P.counters) {
+          atomicAdd(&P.counters[0], (unsigned long long)L.kg);
+          atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)L.kg));
+        }
+      }
+    }
+  }
+  return finish;
+}
+
+// Spread run: the A systems of the warp's holder groups (bits of `holders`, one per
+// group) are copied into groups a R .. a R + R - 1 (system a, replica g % R); the groups
+// beyond A R hold a copy of system 0 and take no part.  Steps until one system finishes;
+// afterwards only replica 0 of each unfinished system keeps it (has), ready for the next
+// layout.
+template <int N, bool JAC, int R>
+__device__ __forceinline__ void mvs_spread_run(const BinView &B, const StepParams &P, MvsLane<ARing<(JAC ? N : N - 1)>::RTA> &L,
+                                               unsigned holders, int A, int g, int b, bool lane_ok,
+                                               unsigned long long &kep_iters) {
+  constexpr int G = 32 / N;
+  const unsigned FULL = 0xffffffffu;
+  const bool used = g < A * R;
+  const int a = used ? g / R : 0;
+  const int rho = used ? g % R : 0;
+  // the a-th holder group
+  unsigned hs = holders;
+  for (int i = 0; i < a; i++) hs &= hs - 1;
+  const int src_group = (__ffs(hs) - 1) / N;
+  mvs_lane_copy(L, src_group * N + b);
+  const int g0 = a * R;
+  const unsigned gset = used ? (R * N >= 32 ? FULL : (((1u << (R * N)) - 1u) << (g0 * N))) : 0u;
+  const int base = g * N;
+  const bool writer = lane_ok && used && rho == 0;
+  (void)G;
+  for (;;) {
+    const bool fin = mvs_stream_step<N, JAC, R>(B, P, L, b, base, rho, g0, gset, writer, kep_iters);
+    if (__any_sync(FULL, fin && used)) {
+      if (fin || !used || rho != 0) L.has = false;
+      return;
+    }
+  }
+}
+
 template <int N, bool JAC>
 __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParams &P) {
   constexpr int G = 32 / N;
   constexpr int MR = JAC ? N : N - 1;
   constexpr int RTA = ARing<MR>::RTA;
   constexpr int RT = ARing<MR>::RT;
-  constexpr unsigned long long NP = JAC ? (unsigned long long)N * (N - 1) / 2 : (unsigned long long)(N - 1) * (N - 2) / 2;
+  // replicas of the spread mode (no more than the ring has rounds): one system left, two
+  constexpr int RS1 = G < RT ? G : (RT > 1 ? RT : 1);
+  constexpr int RS2 = G / 2 < RT ? (G / 2 > 1 ? G / 2 : 1) : (RT > 1 ? RT : 1);
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   int g = lane / N, b = lane - g * N;
@@ -625,29 +880,21 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
   const int SP = B.S_pad;
   const unsigned gm = ((1u << N) - 1u) << base;
 
-  // the group's current system and its constants (group-uniform)
-  int s = 0;
-  bool has = false, exhausted = false;
-  double m = 1.0, m0 = 1.0, Minv = 1.0, eta_prev_inv = 0.0, w = 1.0, mu = 1.0, m0inv = 1.0;
-  KepConst K = kep_const(1.0);
-  double kc[RTA];
-  LaunchPlan plan;
-  plan.N = 0;
-  plan.full = 1;
-  plan.exact = 1;
-  plan.h_last = P.dt;
-  plan.t_end = P.t_end;
-  double t0 = 0.0;
-  int kg = 0;
-  double q[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, acc[3] = {0.0, 0.0, 0.0};
-  double rq = 1.0;  // Jacobi: 1/|q| of the current q (planets)
-  unsigned long long kep_iters = 0;
+  MvsLane<RTA> L;
+  L.K = kep_const(1.0);
+  L.plan.N = 0;
+  L.plan.full = 1;
+  L.plan.exact = 1;
+  L.plan.h_last = P.dt;
+  L.plan.t_end = P.t_end;
 #pragma unroll
-  for (int r = 0; r < RTA; r++) kc[r] = 0.0;
+  for (int r = 0; r < RTA; r++) L.kc[r] = 0.0;
+  bool exhausted = false;
+  unsigned long long kep_iters = 0;
 
   for (;;) {
     // ---- refill: groups without a system take the bin's next one
-    const bool need = !has && !exhausted;
+    const bool need = !L.has && !exhausted;
     if (__any_sync(FULL, need)) {
       int sn = 0;
       if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
@@ -655,7 +902,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       const int ss = stream_system(B, sn);
       const bool take = need && ss >= 0;
       if (need && ss < 0) exhausted = true;
-      const int sl = take ? ss : s;  // a valid row for every lane's loads
+      const int sl = take ? ss : L.s;  // a valid row for every lane's loads
       double xn[3], vn[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -663,18 +910,17 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
         vn[c] = B.v[(size_t)(c * N + b) * SP + sl];
       }
       // constants: recomputed from the same masses for groups that keep their system
-      const double mn = take ? B.m[(size_t)b * SP + sl] : m;
-      m = mn;
-      m0 = shfl(m, base);
-      const double Mtot = grp_sum<N>(m, b, base);
-      Minv = 1.0 / Mtot;
-      const double eta = grp_scan_excl<N>(m, b) + m;
-      const double eta_prev = eta - m;
-      eta_prev_inv = b == 0 ? 0.0 : 1.0 / eta_prev;
-      w = m / eta;
-      mu = JAC ? (b == 0 ? m0 : m0 * eta * eta_prev_inv) : m0;
-      K = kep_const(mu);
-      m0inv = 1.0 / m0;
+      L.m = take ? B.m[(size_t)b * SP + sl] : L.m;
+      L.m0 = shfl(L.m, base);
+      const double Mtot = grp_sum<N>(L.m, b, base);
+      L.Minv = 1.0 / Mtot;
+      const double eta = grp_scan_excl<N>(L.m, b) + L.m;
+      const double eta_prev = eta - L.m;
+      L.eta_prev_inv = b == 0 ? 0.0 : 1.0 / eta_prev;
+      L.w = L.m / eta;
+      L.mu = JAC ? (b == 0 ? L.m0 : L.m0 * eta * L.eta_prev_inv) : L.m0;
+      L.K = kep_const(L.mu);
+      L.m0inv = 1.0 / L.m0;
       {
         const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
 #pragma unroll
@@ -682,126 +928,50 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
           int p = jm + r;
           if (p >= MR) p -= MR;
           const int pl = JAC ? p : p + 1;
-          double mp = shfl(m, base + (JAC ? 0 : 1) + p);
-          kc[r - 1] = (b != 0 && pl != 0 && r <= RT) ? hill_kc(P.ce_factor, m, mp, m0) : 0.0;
+          double mp = shfl(L.m, base + (JAC ? 0 : 1) + p);
+          L.kc[r - 1] = (b != 0 && pl != 0 && r <= RT) ? hill_kc(P.ce_factor, L.m, mp, L.m0) : 0.0;
         }
       }
       double qn[3], un[3];
-      if (JAC) to_jacobi<N>(xn, vn, m, Minv, eta_prev_inv, b, base, qn, un);
-      else to_dh<N>(xn, vn, m, Minv, b, base, qn, un);
+      if (JAC) to_jacobi<N>(xn, vn, L.m, L.Minv, L.eta_prev_inv, b, base, qn, un);
+      else to_dh<N>(xn, vn, L.m, L.Minv, b, base, qn, un);
       double an[3], Qn[3], d2n[RTA];
 #pragma unroll
       for (int r = 0; r < RTA; r++) d2n[r] = 0.0;
       double rqn = 1.0;
-      mvs_acc<N, JAC>(P.fk, qn, m, w, eta_prev_inv, mu, b, base, an, Qn, d2n, rqn);
+      mvs_acc<N, JAC>(P.fk, qn, L.m, L.w, L.eta_prev_inv, L.mu, b, base, an, Qn, d2n, rqn);
       if (take) {
-        rq = rqn;
-        s = ss;
-        const double tn = B.t[s];
-        const bool runnable = B.status[s] <= SWARM_SYS_DONE;
-        plan = launch_plan(B, P, s, tn, runnable);
-        t0 = tn;
-        kg = 0;
+        L.rq = rqn;
+        L.s = ss;
+        const double tn = B.t[L.s];
+        const bool runnable = B.status[L.s] <= SWARM_SYS_DONE;
+        L.plan = launch_plan(B, P, L.s, tn, runnable);
+        L.t0 = tn;
+        L.kg = 0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-          q[c] = qn[c];
-          u[c] = un[c];
-          acc[c] = an[c];
+          L.q[c] = qn[c];
+          L.u[c] = un[c];
+          L.acc[c] = an[c];
         }
-        has = plan.N > 0;
-        if (runnable && plan.N == 0 && lane_ok && b == 0) B.status[s] = SWARM_SYS_DONE;
+        L.has = L.plan.N > 0;
+        if (runnable && L.plan.N == 0 && lane_ok && b == 0) B.status[L.s] = SWARM_SYS_DONE;
       }
       continue;
     }
-    if (!__any_sync(FULL, has)) break;
-
+    const unsigned holders = __ballot_sync(FULL, L.has && lane_ok && b == 0);
+    if (!holders) break;
+    if constexpr (RS1 > 1) {
+      const int A = __popc(holders);
+      if (2 * A <= G && __any_sync(FULL, exhausted)) {
+        if (RS1 > RS2 && A * RS1 <= G) mvs_spread_run<N, JAC, RS1>(B, P, L, holders, A, g, b, lane_ok, kep_iters);
+        else mvs_spread_run<N, JAC, RS2>(B, P, L, holders, A, g, b, lane_ok, kep_iters);
+        exhausted = true;
+        continue;
+      }
+    }
     // ---- one step for every group holding a system
-    const bool active = has;
-    if (active) kg++;
-    const double h = (active && kg == plan.N && !plan.exact) ? plan.h_last : P.dt;
-    const double hh = 0.5 * h;
-    if (!JAC) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; c++)
-        if (b == 0) q[c] = fma(h, u[c], q[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
-    int its = 0;
-    const bool ok = kepler_drift<JAC>(P.fk, active && b != 0, K, q, u, h, its, rq);
-    kep_iters += its;
-    double Q[3], d2[RTA];
-#pragma unroll
-    for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-    mvs_acc<N, JAC, JAC>(P.fk, q, m, w, eta_prev_inv, mu, b, base, acc, Q, d2, rq);
-#pragma unroll
-    for (int c = 0; c < 3; c++) u[c] = fma(hh, acc[c], u[c]);
-    if (!JAC) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, m, u[c]), b, base);
-        q[c] = b == 0 ? fma(hh, u[c], q[c]) : fma(kmul(P.fk, hh, m0inv), ps, q[c]);
-        Q[c] = q[c];
-      }
-    }
-    // monitor on the heliocentric positions at the end of the step
-    const double q2 = fma(Q[2], Q[2], fma(Q[1], Q[1], kmul(P.fk, Q[0], Q[0])));
-    const bool nf = nonfinite(q[0]) | nonfinite(q[1]) | nonfinite(q[2]) | nonfinite(u[0]) | nonfinite(u[1]) |
-                    nonfinite(u[2]);
-    const bool ej = (b != 0) && (P.eject2 > 0.0) && (q2 > P.eject2);
-    bool ce = false;
-    {
-      const int jm = JAC ? b : (b == 0 ? 0 : b - 1);
-#pragma unroll
-      for (int r = 1; r <= RTA; r++) {
-        int p = jm + r;
-        if (p >= MR) p -= MR;
-        double q2p = shfl(q2, base + (JAC ? 0 : 1) + p);
-        if (kc[r - 1] > 0.0 && close_encounter(P.fk, d2[r - 1], kc[r - 1], q2, q2p)) ce = true;
-      }
-    }
-    const unsigned bnf = __ballot_sync(FULL, active && nf) & gm;
-    const unsigned bkn = __ballot_sync(FULL, active && !ok) & gm;
-    const unsigned bej = __ballot_sync(FULL, active && ej) & gm;
-    const unsigned bce = __ballot_sync(FULL, active && ce) & gm;
-    const int code = bkn ? SWARM_SYS_KEPLER_NOCONV
-                         : bnf ? SWARM_SYS_NONFINITE
-                               : bej ? SWARM_SYS_EJECTED : bce ? SWARM_SYS_CLOSE_ENCOUNTER : 0;
-    const bool finish = active && (code != 0 || kg == plan.N);
-    const bool want_log = active && !code && P.log_interval > 0 && (kg % P.log_interval) == 0;
-    if (__any_sync(FULL, finish || want_log)) {
-      double xo[3], vo[3];
-      if (JAC) from_jacobi<N>(q, u, w, b, base, xo, vo);
-      else from_dh<N>(q, u, m, m0, Minv, b, base, xo, vo);
-      const double tk = step_time(plan, kg, t0, P.dt);
-      if (__any_sync(FULL, want_log)) {  // the energy sum is a warp collective
-        double e[4];
-        ring_energy<N>(xo, vo, m, b, base, e);
-        if (want_log && lane_ok && b == 0) write_log(P, B.gidx[s], tk, e);
-      }
-      if (finish && lane_ok) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          B.x[(size_t)(c * N + b) * SP + s] = xo[c];
-          B.v[(size_t)(c * N + b) * SP + s] = vo[c];
-        }
-        if (b == 0) {
-          B.t[s] = tk;
-          B.status[s] = code ? code : (plan.full ? SWARM_SYS_DONE : SWARM_SYS_ACTIVE);
-          if (P.counters) {
-            atomicAdd(&P.counters[0], (unsigned long long)kg);
-            atomicAdd(&P.counters[1], NP * (1ull + (unsigned long long)kg));
-          }
-        }
-      }
-      if (finish) has = false;
-    }
+    if (mvs_stream_step<N, JAC, 1>(B, P, L, b, base, 0, g, gm, lane_ok, kep_iters)) L.has = false;
   }
   if (P.counters && lane_ok && kep_iters) atomicAdd(&P.counters[2], kep_iters);
 }
