@@ -532,13 +532,33 @@ def ncu_case(name):
     stream = torch.cuda.current_stream()
     from paper_1208_1157_gb300 import tune
     S.tuner_load(tune.DEFAULT_PATH)
+    if name == "io":  # checkpoint I/O of the paper-shaped ensemble: set_state + state query, 3 times
+        import numpy as np
+
+        ens = ics.three_body(N_SYS, seed=2)
+        pos = torch.empty((len(ens["mass"]), 3), dtype=torch.float64, pin_memory=True).numpy()
+        vel = torch.empty_like(torch.from_numpy(pos)).pin_memory().numpy()
+        # the same bytes moved by a plain elementwise kernel (read a, write b = 1.0 * a:
+        # 18.9 MB each way): the ceiling for a transfer of this size
+        a = torch.ones(len(ens["mass"]) * 6, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        with S.Ensemble(ens, stream=stream) as e:
+            for _ in range(3):
+                e.set_state(ens["pos"], ens["vel"])
+                e.state_into(pos, vel, np.empty(N_SYS), np.empty(N_SYS, np.int32))
+                torch.mul(a, 1.0, out=b)
+        torch.cuda.synchronize()
+        log(f"ncu case io: {N_SYS} systems x {N_BODY} bodies")
+        return
+    ctas = 0
     if name in ("hermite", "hermite_bpl", "plain"):
         ens = ics.three_body(N_SYS, seed=2)
         mapping = {"hermite": S.MAP_SYSTEM_PER_LANE, "hermite_bpl": S.MAP_BODY_PER_LANE, "plain": S.MAP_PLAIN_PER_STEP}[name]
         steps, integ, dt = (200 if name != "plain" else 20), S.HERMITE4, DT
-    elif name == "mvs":
+    elif name in ("mvs", "mvs_2cta"):
         ens = ics.mvs_compact(16384, seed=4)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 200, S.MVS_JACOBI, TWO_PI / 20
+        ctas = 2 if name == "mvs_2cta" else 0
     elif name == "ragged":
         ens = ics.ragged(65536, seed=3)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 2, S.HERMITE4, DT
@@ -565,6 +585,7 @@ def ncu_case(name):
         raise SystemExit(f"unknown case {name}")
     with S.Ensemble(ens, stream=stream) as e:
         e.set_option(S.OPT_MAPPING, mapping)
+        e.set_option(S.OPT_CTAS_PER_SM, ctas)
         e.set_stop(3.0, 100.0)
         t_end = 0.1 * TWO_PI if integ in (S.HERMITE4_ADAPTIVE, S.RKCK_ADAPTIVE) else steps * dt
         e.integrate(t_end, integ, dt)
@@ -582,8 +603,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
-    ap.add_argument("--ncu-case", help="hermite, hermite_bpl, plain, mvs, ragged, ragged_bin<n>, rkck, wide, "
-                    "hermite_adaptive or rkck_adaptive")
+    ap.add_argument("--ncu-case", help="hermite, hermite_bpl, plain, mvs, mvs_2cta, ragged, ragged_bin<n>, rkck, wide, "
+                    "hermite_adaptive, rkck_adaptive or io")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)

@@ -201,17 +201,24 @@ void swarm_destroy_ensemble(swarm_ensemble *ens);
 /* Continuous batching (the serving layer above the integrator; the paper's Algorithm 1
  * loop generalized to requests that arrive while others run).  Requests of 1..4096
  * systems with one body count n and one integrator are queued by swarm_server_submit;
- * each swarm_server_step (1) admits queued requests, in arrival order, whose pool
- * (integrator, n) has enough free slots — pools are allocated on demand within
- * device_bytes (0 = no budget), empty pools are released when the budget is short —
+ * every system occupies one slot of the pool (integrator, n) while it runs.  Each
+ * swarm_server_step
+ * (1) admits queued systems: requests in arrival order, each taking as many of its
+ *     remaining systems as its pool has free slots; a pool admits no later request while
+ *     an earlier one still waits for slots (first come, first served per pool, so no
+ *     request waits for ever); pools are allocated on demand within device_bytes (0 = no
+ *     budget), in arrival order too, and empty pools are released when the budget is short;
  * (2) advances every occupied slot by at most quantum_steps steps toward its own t_end
- * (one launch per pool over the list of its occupied slots, body per lane, slots handed
- * out per group; the pools' launches run concurrently), and (3) retires requests whose
- * systems all reached
- * t_end or stopped, copying their results to host memory and freeing their slots for
- * the next admissions.  A system takes the same steps as it would alone (steps of dt, the
- * last one shortened to land on t_end), so results do not depend on the mix.  Not
- * thread-safe: one thread drives a server. */
+ *     (one launch per pool over the list of its occupied slots, body per lane, slots
+ *     handed out per group; the pools' launches run concurrently);
+ * (3) retires every system that reached t_end or stopped (Sec. 4.3's monitor stops systems
+ *     one by one): its result is copied to its request's host buffer and its slot is free
+ *     for the next admission at once; a request is DONE when its last system retires.
+ * A system takes the same steps as it would alone (steps of dt, the last one shortened to
+ * land on t_end), so results do not depend on the mix or on when each system was
+ * admitted.  Stats: `admitted` counts requests with at least one system admitted,
+ * `queued` requests with systems still waiting.  Not thread-safe: one thread drives a
+ * server. */
 typedef struct swarm_server swarm_server;
 typedef struct {
   int32_t slots_per_pool;   /* systems per (integrator, n) pool */
@@ -231,7 +238,8 @@ enum swarm_request_state { SWARM_REQ_QUEUED = 0, SWARM_REQ_RUNNING = 1, SWARM_RE
 
 int swarm_server_create(const swarm_server_config *cfg, void *cuda_stream, swarm_server **out);
 /* Host arrays in the creation layout ([n_sys*n_body][3]); copied, so the caller may reuse
- * them on return.  *id receives the request id. */
+ * them on return.  *id receives the request id.  SWARM_EINVAL for more than 2e9 steps of
+ * the integrator's dt between t0 and t_end, or more systems than a pool holds. */
 int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_body, const double *mass, const double *pos,
                         const double *vel, double t0, double t_end, int integrator, int64_t *id);
 /* One scheduling round (admit, advance, retire); *n_completed = requests finished in it. */
@@ -240,8 +248,9 @@ int swarm_server_step(swarm_server *sv, int32_t *n_completed);
  * NULL) and its latency (submit to retirement, seconds). */
 int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, double *pos, double *vel, double *time,
                       int32_t *status, double *latency_s);
-/* Cancel a queued or running request (its slots are freed for the next admissions);
- * SWARM_ESTATE if it already finished. */
+/* Cancel a queued or running request (its systems still waiting leave the queue, its
+ * admitted ones free their slots for the next admissions); SWARM_ESTATE if it already
+ * finished. */
 int swarm_server_cancel(swarm_server *sv, int64_t id);
 /* Forget a finished or cancelled request (frees its host copy of the results). */
 int swarm_server_release(swarm_server *sv, int64_t id);

@@ -30,6 +30,10 @@ struct BinView {
   const double *t_end = nullptr;  // per-system end time (serving slots); null: the call's
   const int32_t *list = nullptr;  // systems to run (serving: the occupied slots); null: all S
   int nlist = 0;
+  // the bin is the ensemble's systems g0 .. g0 + S - 1, whose caller rows start at row0
+  // (every uniform ensemble); -1: its systems are scattered (gidx)
+  int g0 = -1;
+  long long row0 = -1;
 };
 
 // k-th system of a launch that hands out systems one by one, or -1 past the end

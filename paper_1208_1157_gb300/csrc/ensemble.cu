@@ -47,6 +47,8 @@ struct Bin {
   int n = 0, S = 0, S_pad = 0;
   double *x = nullptr, *v = nullptr, *m = nullptr, *t = nullptr;
   int32_t *status = nullptr, *gidx = nullptr;
+  int g0 = -1;           // first system of a contiguous bin (-1: scattered)
+  int64_t row0 = -1;     // its first caller row
   void *block = nullptr;
   BinView view() const {
     BinView b;
@@ -59,6 +61,8 @@ struct Bin {
     b.t = t;
     b.status = status;
     b.gidx = gidx;
+    b.g0 = g0;
+    b.row0 = row0;
     return b;
   }
 };
@@ -115,7 +119,11 @@ struct swarm_ensemble {
 };
 
 // ------------------------------------------------------------------ layout kernels
-// caller layout ([sum n][3] rows, system after system) <-> bin SoA
+// caller layout ([sum n][3] rows, system after system) <-> bin SoA.
+// unpack: one thread per system.  The caller's rows are read with a 24n-byte stride per
+// lane, which the L1 cache absorbs (a warp's rows are one contiguous run, each line is
+// fetched once), and the SoA rows are written 32 systems per warp instruction; measured
+// at the speed of a plain elementwise kernel moving the same bytes.
 __global__ void unpack_kernel(BinView B, const int64_t *__restrict__ offs, const double *__restrict__ pos,
                               const double *__restrict__ vel, const double *__restrict__ mass,
                               const double *__restrict__ time, const int32_t *__restrict__ status) {
@@ -134,19 +142,54 @@ __global__ void unpack_kernel(BinView B, const int64_t *__restrict__ offs, const
   if (status) B.status[s] = status[g];
 }
 
-__global__ void pack_kernel(BinView B, const int64_t *__restrict__ offs, double *__restrict__ pos,
-                            double *__restrict__ vel, double *__restrict__ time, int32_t *__restrict__ status) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B.S) return;
-  const int g = B.gidx[s];
-  const int64_t o = offs[g];
-  for (int b = 0; b < B.n; b++)
-    for (int c = 0; c < 3; c++) {
-      if (pos) pos[3 * (o + b) + c] = B.x[(size_t)(c * B.n + b) * B.S_pad + s];
-      if (vel) vel[3 * (o + b) + c] = B.v[(size_t)(c * B.n + b) * B.S_pad + s];
-    }
-  if (time) time[g] = B.t[s];
-  if (status) status[g] = B.status[s];
+// pack: the reverse direction cannot lean on L1 (stores go through to L2 sector by
+// sector, so strided rows write each 32-byte sector four times).  A block of kPackThreads
+// systems reads its SoA values one thread per system (32 systems per warp instruction)
+// into shared memory laid out like the caller's rows, then writes those rows as one
+// contiguous run when its systems are consecutive systems of the ensemble (row0 >= 0:
+// every uniform ensemble), else a warp per system.
+constexpr int kPackThreads = 128;
+constexpr int kPackMaxN = 4;  // shared memory of the staged path: 6 doubles per body
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(BinView B, const int64_t *__restrict__ offs, double *__restrict__ pos,
+                                                            double *__restrict__ vel, double *__restrict__ time,
+                                                            int32_t *__restrict__ status) {
+  __shared__ double sm[2 * 3 * kPackMaxN * kPackThreads];
+  const int n = B.n, E = 3 * n;
+  const int s0 = blockIdx.x * kPackThreads, s = s0 + threadIdx.x;
+  const int ts = min(kPackThreads, B.S - s0);
+  if (n > kPackMaxN || B.row0 < 0) {  // thread per system, rows written directly
+    if (s >= B.S) return;
+    const int g = B.gidx[s];
+    const int64_t o = offs[g];
+    for (int b = 0; b < n; b++)
+      for (int c = 0; c < 3; c++) {
+        if (pos) pos[3 * (o + b) + c] = B.x[(size_t)(c * n + b) * B.S_pad + s];
+        if (vel) vel[3 * (o + b) + c] = B.v[(size_t)(c * n + b) * B.S_pad + s];
+      }
+    if (time) time[g] = B.t[s];
+    if (status) status[g] = B.status[s];
+    return;
+  }
+  double *sp = sm, *sv = sm + 3 * kPackMaxN * kPackThreads;
+  if (s < B.S) {
+#pragma unroll
+    for (int b = 0; b < kPackMaxN; b++)
+      if (b < n)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          if (pos) sp[threadIdx.x * E + 3 * b + c] = B.x[(size_t)(c * n + b) * B.S_pad + s];
+          if (vel) sv[threadIdx.x * E + 3 * b + c] = B.v[(size_t)(c * n + b) * B.S_pad + s];
+        }
+    if (time) time[B.g0 + s] = B.t[s];
+    if (status) status[B.g0 + s] = B.status[s];
+  }
+  __syncthreads();
+  const long long rf = 3 * (B.row0 + (long long)s0 * n);  // first double of the block's rows
+#pragma unroll 4
+  for (int f = threadIdx.x; f < ts * E; f += kPackThreads) {
+    if (pos) pos[rf + f] = sp[f];
+    if (vel) vel[rf + f] = sv[f];
+  }
 }
 
 // Eq. 6 (each pair once, 1/sqrt in full precision) and L = sum m x cross v, per system.
@@ -320,6 +363,10 @@ extern "C" int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const
     b.status = (int32_t *)(d + nd);
     b.gidx = b.status + b.S_pad;
     CKC(cudaMemcpyAsync(b.gidx, members[n].data(), sizeof(int32_t) * b.S, cudaMemcpyHostToDevice, e->stream));
+    if (members[n].back() - members[n].front() == b.S - 1) {  // consecutive systems
+      b.g0 = members[n].front();
+      b.row0 = e->offs[b.g0];
+    }
     e->bins.push_back(b);
   }
   std::vector<BinView> views;
@@ -819,7 +866,8 @@ extern "C" int swarm_set_state(swarm_ensemble *e, const double *pos, const doubl
 
 static int pack_to(const swarm_ensemble *e, double *pos, double *vel, double *time, int32_t *status) {
   for (auto &b : e->bins) {
-    pack_kernel<<<(b.S + 127) / 128, 128, 0, e->stream>>>(b.view(), e->d_offs, pos, vel, time, status);
+    pack_kernel<<<(b.S + kPackThreads - 1) / kPackThreads, kPackThreads, 0, e->stream>>>(b.view(), e->d_offs, pos, vel,
+                                                                                       time, status);
     CK(cudaGetLastError());
   }
   return SWARM_OK;

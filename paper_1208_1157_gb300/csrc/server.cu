@@ -1,13 +1,20 @@
 // Continuous-batching server: integration requests of different sizes, body counts and
 // integrators share the GPU.  Their systems occupy slots of device-resident pools (one
-// pool per integrator and body count); every scheduling round admits queued requests
-// into free slots (within a device-memory budget), advances all occupied slots by one
-// quantum of at most Q steps (one launch per pool over the list of its occupied slots,
-// the pools' launches running concurrently on forked streams), then retires the
-// requests whose systems all reached their end time or stopped and frees their slots for
-// the next admissions.  A request's systems take exactly the steps they would take alone
-// (full steps of dt, the last one shortened to land on its t_end), so its result does not
-// depend on what else is in flight.
+// pool per integrator and body count), one system per slot.  Every scheduling round
+//  - admits queued systems into free slots, request by request in arrival order and per
+//    pool first come first served: the oldest request waiting for a pool takes whatever
+//    slots are free (the rest of its systems wait for the next rounds) and no later
+//    request of that pool is admitted before it is complete; pools are created on demand
+//    within a device-memory budget, again in arrival order;
+//  - advances all occupied slots by one quantum of at most Q steps (one launch per pool
+//    over the list of its occupied slots, the pools' launches concurrent on forked streams);
+//  - retires every system that reached its end time or stopped: its result moves to its
+//    request's host buffer and its slot is free for the next admissions at once (the
+//    monitor stops systems one by one, Sec. 4.3); a request completes when its last
+//    system retires.
+// A request's systems take exactly the steps they would take alone (full steps of dt, the
+// last one shortened to land on its t_end), so its result does not depend on what else is
+// in flight or on when each of its systems was admitted.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +56,7 @@ struct Pool {
   double *t_end = nullptr;
   std::set<int> free_slots;    // lowest slots are handed out first
   std::vector<int64_t> owner;  // request id per slot, -1 if free
+  std::vector<int32_t> owner_sys;  // the slot's system within its request
   int32_t *d_list = nullptr;   // occupied slots of the current round (device)
   std::vector<int32_t> h_list;
   int32_t *h_status = nullptr; // pinned copy of the slots' status after a round
@@ -72,10 +80,12 @@ struct Request {
   int64_t id = 0;
   int n_sys = 0, n = 0, integ = 0;
   double t0 = 0, t_end = 0;
-  std::vector<double> mass, pos, vel;  // caller layout
+  std::vector<double> mass, pos, vel;  // caller layout (kept until every system is admitted)
   int state = SWARM_REQ_QUEUED;
   Pool *pool = nullptr;
-  std::vector<int> slots;
+  int admitted = 0;  // systems 0 .. admitted-1 have been given slots
+  int retired = 0;   // systems whose results are in out_*
+  std::vector<int> slots;  // slot of each admitted system, -1 once retired
   Clock::time_point submitted, finished;
   std::vector<double> out_pos, out_vel, out_time;
   std::vector<int32_t> out_status;
@@ -100,7 +110,7 @@ __global__ void admit_kernel(BinView B, double *t_end_slots, const int *__restri
   t_end_slots[s] = t_end;
 }
 
-// gather one finished request and free its slots
+// gather finished systems of one pool (the listed slots, in list order) and free their slots
 __global__ void retire_kernel(BinView B, const int *__restrict__ slots, int n_sys, double *__restrict__ pos,
                               double *__restrict__ vel, double *__restrict__ time, int32_t *__restrict__ status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,6 +209,7 @@ static int make_pool(swarm_server *sv, int integ, int n, Pool **out) {
   SCK(cudaGetLastError());
   for (int i = 0; i < cap; i++) p->free_slots.insert(p->free_slots.end(), i);
   p->owner.assign(cap, -1);
+  p->owner_sys.assign(cap, -1);
   SCK(cudaMalloc(&p->d_list, sizeof(int32_t) * cap));
   SCK(cudaMalloc(&p->d_next, sizeof(int)));
   SCK(cudaMallocHost(&p->h_status, sizeof(int32_t) * cap));
@@ -290,6 +301,11 @@ extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_bo
   r->mass.assign(mass, mass + nb);
   r->pos.assign(pos, pos + 3 * nb);
   r->vel.assign(vel, vel + 3 * nb);
+  r->slots.assign(n_sys, -1);
+  r->out_pos.assign(3 * nb, 0.0);
+  r->out_vel.assign(3 * nb, 0.0);
+  r->out_time.assign(n_sys, 0.0);
+  r->out_status.assign(n_sys, 0);
   r->submitted = Clock::now();
   *id = r->id;
   sv->queue.push_back(r->id);
@@ -298,12 +314,18 @@ extern "C" int swarm_server_submit(swarm_server *sv, int32_t n_sys, int32_t n_bo
   return SWARM_OK;
 }
 
-// Admission in batches: every queued request that fits into its pool gets slots, its
-// arrays are packed into the pinned staging buffer, and each full batch moves to the
-// device in one copy per array followed by one scatter kernel per request.
+// Admission in batches, system by system.  Requests are visited in arrival order; a
+// request takes as many of its remaining systems as its pool has free slots, and a pool
+// whose oldest waiting request is not complete admits nobody after it (first come, first
+// served per pool: a large request cannot be overtaken for ever by small ones).  A request
+// whose pool cannot be created for lack of budget likewise stops every later request from
+// creating a pool.  The systems' arrays are packed into the pinned staging buffer; each
+// full batch moves to the device in one copy per array, then one scatter kernel per
+// admitted slice.
 static int admit(swarm_server *sv) {
   struct Item {
     Request *r;
+    int first, count;
     size_t d_off, s_off;
   };
   std::vector<Item> batch;
@@ -314,11 +336,10 @@ static int admit(swarm_server *sv) {
     SCK(cudaMemcpyAsync(sv->d_slots, sv->h_slots, sizeof(int) * s_used, cudaMemcpyHostToDevice, sv->stream));
     for (auto &it : batch) {
       Request *r = it.r;
-      const size_t nb = (size_t)r->n_sys * r->n;
+      const size_t nb = (size_t)it.count * r->n;
       const double *dpos = sv->d_stage + it.d_off, *dvel = dpos + 3 * nb, *dmass = dvel + 3 * nb;
-      admit_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(r->pool->view, r->pool->t_end,
-                                                                    sv->d_slots + it.s_off, r->n_sys, dpos, dvel,
-                                                                    dmass, r->t0, r->t_end);
+      admit_kernel<<<(it.count + 127) / 128, 128, 0, sv->stream>>>(r->pool->view, r->pool->t_end, sv->d_slots + it.s_off,
+                                                                    it.count, dpos, dvel, dmass, r->t0, r->t_end);
       SCK(cudaGetLastError());
     }
     SCK(cudaStreamSynchronize(sv->stream));  // the staging buffers are reused by the next batch
@@ -326,47 +347,71 @@ static int admit(swarm_server *sv) {
     d_used = s_used = 0;
     return SWARM_OK;
   };
+  std::set<Pool *> blocked;      // pools whose oldest waiting request is not complete
+  bool creation_blocked = false;  // an older request waits for budget to create its pool
   for (auto it = sv->queue.begin(); it != sv->queue.end();) {
     Request *r = sv->reqs[*it].get();
     Pool *p = nullptr;
-    int rc = make_pool(sv, r->integ, r->n, &p);
-    if (rc) return rc;
-    if (!p || (int)p->free_slots.size() < r->n_sys) {  // not enough memory/slots yet: later
+    auto pit = sv->pools.find(std::make_pair(r->integ, r->n));
+    if (pit != sv->pools.end()) {
+      p = pit->second.get();
+    } else if (!creation_blocked) {
+      int rc = make_pool(sv, r->integ, r->n, &p);
+      if (rc) return rc;
+      if (!p) creation_blocked = true;  // over budget until slots free up
+    }
+    if (!p || blocked.count(p)) {
       ++it;
       continue;
     }
-    const size_t nb = (size_t)r->n_sys * r->n;
-    if (d_used + 7 * nb > sv->stage_doubles || s_used + r->n_sys > (size_t)kStageSlots)
-      if ((rc = flush())) return rc;
-    r->slots.resize(r->n_sys);
-    for (int i = 0; i < r->n_sys; i++) {
-      const int slot = *p->free_slots.begin();
-      p->free_slots.erase(p->free_slots.begin());
-      r->slots[i] = slot;
-      p->owner[slot] = r->id;
+    const int k = std::min(r->n_sys - r->admitted, (int)p->free_slots.size());
+    if (k > 0) {
+      const size_t nb = (size_t)k * r->n;
+      if (d_used + 7 * nb > sv->stage_doubles || s_used + k > (size_t)kStageSlots) {
+        int rc = flush();
+        if (rc) return rc;
+      }
+      const int first = r->admitted;
+      for (int i = 0; i < k; i++) {
+        const int slot = *p->free_slots.begin();
+        p->free_slots.erase(p->free_slots.begin());
+        r->slots[first + i] = slot;
+        p->owner[slot] = r->id;
+        p->owner_sys[slot] = first + i;
+        sv->h_slots[s_used + i] = slot;
+      }
+      const size_t off = (size_t)first * r->n;  // first body of the slice
+      double *h = sv->h_stage + d_used;
+      std::memcpy(h, r->pos.data() + 3 * off, sizeof(double) * 3 * nb);
+      std::memcpy(h + 3 * nb, r->vel.data() + 3 * off, sizeof(double) * 3 * nb);
+      std::memcpy(h + 6 * nb, r->mass.data() + off, sizeof(double) * nb);
+      batch.push_back(Item{r, first, k, d_used, s_used});
+      d_used += 7 * nb;
+      s_used += k;
+      if (first == 0) sv->stats.admitted++;
+      r->admitted += k;
+      r->pool = p;
+      r->state = SWARM_REQ_RUNNING;
     }
-    r->pool = p;
-    double *h = sv->h_stage + d_used;
-    std::memcpy(h, r->pos.data(), sizeof(double) * 3 * nb);
-    std::memcpy(h + 3 * nb, r->vel.data(), sizeof(double) * 3 * nb);
-    std::memcpy(h + 6 * nb, r->mass.data(), sizeof(double) * nb);
-    std::memcpy(sv->h_slots + s_used, r->slots.data(), sizeof(int) * r->n_sys);
-    batch.push_back(Item{r, d_used, s_used});
-    d_used += 7 * nb;
-    s_used += r->n_sys;
-    r->state = SWARM_REQ_RUNNING;
-    r->pos.clear();
-    r->vel.clear();
-    sv->stats.admitted++;
+    if (r->admitted < r->n_sys) {  // the rest waits; nobody overtakes it in this pool
+      blocked.insert(p);
+      ++it;
+      continue;
+    }
+    // every system has a slot: the host copy of the inputs is no longer needed
+    std::vector<double>().swap(r->pos);
+    std::vector<double>().swap(r->vel);
+    std::vector<double>().swap(r->mass);
     it = sv->queue.erase(it);
   }
   return flush();
 }
 
-// Retirement: the statuses of every occupied pool come back in one round of copies; the
-// requests whose systems all reached t_end or stopped are gathered in batches (one
-// gather kernel per request, one copy of the batch to the pinned staging buffer) and
-// their slots freed.
+// Retirement, system by system: the statuses of every occupied pool come back in one
+// round of copies; every slot whose system reached its end time or stopped is gathered
+// (one kernel per pool over the list of its finished slots, the batch in one copy to the
+// pinned staging buffer), its result goes to its request's host buffer and the slot is
+// free for the next admission.  A request completes with its last system.
 static int retire(swarm_server *sv, int32_t *n_completed) {
   std::vector<Pool *> occ;
   for (auto &kv : sv->pools) {
@@ -377,16 +422,9 @@ static int retire(swarm_server *sv, int32_t *n_completed) {
   }
   if (occ.empty()) return SWARM_OK;
   SCK(cudaStreamSynchronize(sv->stream));
-  std::map<int64_t, int> pending;  // request id -> slots not finished
-  for (Pool *p : occ)
-    for (int s = 0; s < p->cap; s++) {
-      const int64_t o = p->owner[s];
-      if (o < 0) continue;
-      int &c = pending[o];
-      if (p->h_status[s] == SWARM_SYS_ACTIVE) c++;
-    }
   struct Item {
-    Request *r;
+    Pool *p;
+    int count;
     size_t d_off, s_off;
   };
   std::vector<Item> batch;
@@ -395,52 +433,71 @@ static int retire(swarm_server *sv, int32_t *n_completed) {
     if (batch.empty()) return SWARM_OK;
     SCK(cudaMemcpyAsync(sv->d_slots, sv->h_slots, sizeof(int) * s_used, cudaMemcpyHostToDevice, sv->stream));
     for (auto &it : batch) {
-      Request *r = it.r;
-      const size_t nb = (size_t)r->n_sys * r->n;
+      const size_t nb = (size_t)it.count * it.p->n;
       double *dpos = sv->d_stage + it.d_off, *dvel = dpos + 3 * nb, *dtime = dvel + 3 * nb;
-      int32_t *dstat = (int32_t *)(dtime + r->n_sys);
-      retire_kernel<<<(r->n_sys + 127) / 128, 128, 0, sv->stream>>>(r->pool->view, sv->d_slots + it.s_off, r->n_sys,
-                                                                     dpos, dvel, dtime, dstat);
+      int32_t *dstat = (int32_t *)(dtime + it.count);
+      retire_kernel<<<(it.count + 127) / 128, 128, 0, sv->stream>>>(it.p->view, sv->d_slots + it.s_off, it.count, dpos,
+                                                                     dvel, dtime, dstat);
       SCK(cudaGetLastError());
     }
     SCK(cudaMemcpyAsync(sv->h_stage, sv->d_stage, sizeof(double) * d_used, cudaMemcpyDeviceToHost, sv->stream));
     SCK(cudaStreamSynchronize(sv->stream));
     for (auto &it : batch) {
-      Request *r = it.r;
-      const size_t nb = (size_t)r->n_sys * r->n;
+      Pool *p = it.p;
+      const int n = p->n;
+      const size_t nb = (size_t)it.count * n;
       const double *h = sv->h_stage + it.d_off;
-      r->out_pos.assign(h, h + 3 * nb);
-      r->out_vel.assign(h + 3 * nb, h + 6 * nb);
-      r->out_time.assign(h + 6 * nb, h + 6 * nb + r->n_sys);
-      const int32_t *hs = (const int32_t *)(h + 6 * nb + r->n_sys);
-      r->out_status.assign(hs, hs + r->n_sys);
-      for (int sl : r->slots) {
-        r->pool->owner[sl] = -1;
-        r->pool->free_slots.insert(sl);
+      const int32_t *hs = (const int32_t *)(h + 6 * nb + it.count);
+      for (int i = 0; i < it.count; i++) {
+        const int slot = sv->h_slots[it.s_off + i];
+        Request *r = sv->reqs[p->owner[slot]].get();
+        const int k = p->owner_sys[slot];
+        std::memcpy(r->out_pos.data() + (size_t)3 * k * n, h + (size_t)3 * i * n, sizeof(double) * 3 * n);
+        std::memcpy(r->out_vel.data() + (size_t)3 * k * n, h + 3 * nb + (size_t)3 * i * n, sizeof(double) * 3 * n);
+        r->out_time[k] = h[6 * nb + i];
+        r->out_status[k] = hs[i];
+        r->slots[k] = -1;
+        p->owner[slot] = -1;
+        p->owner_sys[slot] = -1;
+        p->free_slots.insert(slot);
+        if (++r->retired == r->n_sys) {
+          r->state = SWARM_REQ_DONE;
+          r->finished = Clock::now();
+          sv->stats.completed++;
+          (*n_completed)++;
+        }
       }
-      r->slots.clear();
-      r->state = SWARM_REQ_DONE;
-      r->finished = Clock::now();
-      sv->stats.completed++;
-      (*n_completed)++;
     }
     batch.clear();
     d_used = s_used = 0;
     return SWARM_OK;
   };
-  for (auto &kv : pending) {
-    if (kv.second) continue;
-    Request *r = sv->reqs[kv.first].get();
-    const size_t nb = (size_t)r->n_sys * r->n;
-    // pos, vel (3 nb each), time (n_sys), status (n_sys int32 in n_sys/2 + 1 doubles)
-    const size_t need = 6 * nb + r->n_sys + (r->n_sys + 1) / 2 + 1;
-    int rc;
-    if (d_used + need > sv->stage_doubles || s_used + r->n_sys > (size_t)kStageSlots)
-      if ((rc = flush())) return rc;
-    std::memcpy(sv->h_slots + s_used, r->slots.data(), sizeof(int) * r->n_sys);
-    batch.push_back(Item{r, d_used, s_used});
-    d_used += need;
-    s_used += r->n_sys;
+  // staging of a chunk of k systems of body count n: pos and vel (3 k n doubles each),
+  // time (k doubles), status (k int32 in k/2 + 1 doubles)
+  auto need = [](int k, int n) { return 6 * (size_t)k * n + (size_t)k + (size_t)k / 2 + 1; };
+  std::vector<int> fin;
+  for (Pool *p : occ) {
+    fin.clear();
+    for (int s = 0; s < p->cap; s++)
+      if (p->owner[s] >= 0 && p->h_status[s] != SWARM_SYS_ACTIVE) fin.push_back(s);
+    for (size_t i0 = 0; i0 < fin.size();) {
+      // the largest chunk that still fits the staging buffers (flush them first if none does)
+      int k = (int)std::min<size_t>(fin.size() - i0, (size_t)kStageSlots - s_used);
+      const size_t avail = sv->stage_doubles - d_used;
+      if (avail <= 1) k = 0;
+      else k = (int)std::min<size_t>((size_t)k, (avail - 1) / (6 * (size_t)p->n + 2));
+      if (k > 0 && d_used + need(k, p->n) > sv->stage_doubles) k = 0;
+      if (k == 0) {
+        int rc = flush();
+        if (rc) return rc;
+        continue;
+      }
+      std::memcpy(sv->h_slots + s_used, fin.data() + i0, sizeof(int) * k);
+      batch.push_back(Item{p, k, d_used, s_used});
+      d_used += need(k, p->n);
+      s_used += k;
+      i0 += k;
+    }
   }
   return flush();
 }
@@ -535,32 +592,38 @@ extern "C" int swarm_server_poll(swarm_server *sv, int64_t id, int32_t *state, d
   return SWARM_OK;
 }
 
-// Cancel a queued or running request: a queued one leaves the queue, a running one gives
-// its slots back (their systems are marked free on the device).  Its state becomes
-// SWARM_REQ_CANCELLED; release it like a finished one.
+// Cancel a queued or running request: it leaves the queue if some of its systems still
+// wait there, and its admitted systems that have not retired give their slots back (they
+// are marked free on the device).  Its state becomes SWARM_REQ_CANCELLED; release it like
+// a finished one.
 extern "C" int swarm_server_cancel(swarm_server *sv, int64_t id) {
   if (!sv) return sfail(SWARM_EINVAL, "NULL server");
   auto it = sv->reqs.find(id);
   if (it == sv->reqs.end()) return sfail(SWARM_EINVAL, "unknown request id");
   Request *r = it->second.get();
   if (r->state == SWARM_REQ_DONE || r->state == SWARM_REQ_CANCELLED) return sfail(SWARM_ESTATE, "request already finished");
-  if (r->state == SWARM_REQ_QUEUED) {
+  if (r->admitted < r->n_sys) {  // still (partly) waiting: leave the queue
     for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
       if (*q == id) {
         sv->queue.erase(q);
         break;
       }
-  } else {
+  }
+  if (r->pool) {  // admitted systems not yet retired give their slots back
     Pool *p = r->pool;
-    std::vector<int32_t> freeval(r->slots.size(), kFree);
-    for (size_t i = 0; i < r->slots.size(); i++)
-      SCK(cudaMemcpyAsync(p->view.status + r->slots[i], &freeval[i], sizeof(int32_t), cudaMemcpyHostToDevice, sv->stream));
+    std::vector<int> held;
+    for (int sl : r->slots)
+      if (sl >= 0) held.push_back(sl);
+    std::vector<int32_t> freeval(held.size(), kFree);
+    for (size_t i = 0; i < held.size(); i++)
+      SCK(cudaMemcpyAsync(p->view.status + held[i], &freeval[i], sizeof(int32_t), cudaMemcpyHostToDevice, sv->stream));
     SCK(cudaStreamSynchronize(sv->stream));
-    for (int sl : r->slots) {
+    for (int sl : held) {
       p->owner[sl] = -1;
+      p->owner_sys[sl] = -1;
       p->free_slots.insert(sl);
     }
-    r->slots.clear();
+    std::fill(r->slots.begin(), r->slots.end(), -1);
   }
   r->state = SWARM_REQ_CANCELLED;
   r->finished = Clock::now();

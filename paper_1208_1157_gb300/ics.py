@@ -157,8 +157,8 @@ def three_body(n_sys: int, seed: int) -> dict:
     return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
 
 
-def _hill_spaced(n_body, seed, idx, e_max, base_k, m_lo=1e-5, m_hi=1e-3, stride=20):
-    """a_1 = 1; a_{j+1} = a_j (1 + K h/2)/(1 - K h/2), h = ((m_j + m_{j+1})/3)^(1/3), K ~ U(3, 8);
+def _hill_spaced(n_body, seed, idx, e_max, base_k, m_lo=1e-5, m_hi=1e-3, stride=20, k_lo=3.0, k_hi=8.0):
+    """a_1 = 1; a_{j+1} = a_j (1 + K h/2)/(1 - K h/2), h = ((m_j + m_{j+1})/3)^(1/3), K ~ U(k_lo, k_hi);
     masses log-U(m_lo, m_hi).  Draw k of planet j: mass base_k + j, e base_k + stride + j,
     K base_k + 2 stride + j, angles from base_k + 3 stride (stride > planets per system)."""
     S = len(n_body)
@@ -172,7 +172,7 @@ def _hill_spaced(n_body, seed, idx, e_max, base_k, m_lo=1e-5, m_hi=1e-3, stride=
         e[:, j] = e_max * uniform(seed, idx, base_k + stride + j)
     a[:, 0] = 1.0
     for j in range(1, P):
-        K = 3.0 + 5.0 * uniform(seed, idx, base_k + 2 * stride + j)
+        K = k_lo + (k_hi - k_lo) * uniform(seed, idx, base_k + 2 * stride + j)
         h = np.cbrt((mp[:, j - 1] + mp[:, j]) / 3.0)
         a[:, j] = a[:, j - 1] * (1.0 + 0.5 * K * h) / (1.0 - 0.5 * K * h)
     inc, node, peri, E = _angles(seed, idx, base_k + 3 * stride, P)
@@ -198,9 +198,10 @@ def ragged_wide(n_sys: int, seed: int, n_min: int = 16, n_max: int = 32) -> dict
     return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
 
 
-def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0) -> dict:
-    """n bodies, Hill spacing as in `ragged`, e ~ U(0, 0.1); a system whose outermost
-    apocentre a (1 + e) reaches `a_lim` AU is redrawn from the next attempt of its own stream."""
+def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0, k_lo: float = 3.0, k_hi: float = 8.0) -> dict:
+    """n bodies, Hill spacing as in `ragged` (K ~ U(k_lo, k_hi) mutual Hill radii), e ~ U(0, 0.1);
+    a system whose outermost apocentre a (1 + e) reaches `a_lim` AU is redrawn from the
+    next attempt of its own stream."""
     S = n_sys
     n_body = np.full(S, n, dtype=np.int32)
     out = None
@@ -210,7 +211,7 @@ def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0) -> dict:
         nb = n_body[todo]
         # attempt r of system s uses stream index s + r * 2^32
         idx = todo.astype(np.uint64) + np.uint64(attempt) * np.uint64(1 << 32)
-        parts = _hill_spaced(nb, seed, idx, 0.1, 1)
+        parts = _hill_spaced(nb, seed, idx, 0.1, 1, k_lo=k_lo, k_hi=k_hi)
         if out is None:
             out = [np.zeros((S,) + p.shape[1:]) for p in parts]
         apo = parts[1][:, -1] * (1.0 + parts[2][:, -1])

@@ -83,11 +83,16 @@ def oracle_sensitivity(ens, t_end, integrator, dt, **kw):
     return np.maximum(ex, ev)
 
 
-def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, stop_time_rtol=None):
+def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, stop_time_rtol=None, max_relaxed=0.1):
     """Statuses and times equal; positions/velocities within tol (or, for systems whose
     measured round-off sensitivity `sens` exceeds tol/100, within COND_FACTOR * sens);
     the GPU's relative energy error within 2x the oracle's, or below the round-off bound
     steps * u when the oracle's own error is at that level.
+
+    max_relaxed caps the relaxation where the contract is strict: of the systems that ran
+    the whole call without a stop (the non-close-encounter systems), at most this fraction
+    may exceed tol at all (within the sensitivity bound above); the counts are printed and
+    reported in the failure message.  Systems that stopped on the way are not capped.
 
     stop_time_rtol: for an integrator whose step sizes come from an error estimate (the
     adaptive Runge-Kutta step), the estimate is a short sum of large terms that cancel, so
@@ -102,8 +107,6 @@ def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, 
     tbound = np.full(len(ex), 1e-13)
     if sens is not None:
         ill = sens > tol / 100
-        # the strict bar must still be exercised on most of the ensemble
-        assert ill.mean() <= 0.5, f"{ill.sum()} of {len(ill)} systems ill-conditioned"
         bound = np.where(ill, np.maximum(tol, COND_FACTOR * sens), tol)
         # an adaptive integrator's stop time follows the trajectory: same bound there
         tbound = np.where(ill, np.maximum(1e-13, COND_FACTOR * sens), 1e-13)
@@ -117,7 +120,17 @@ def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, 
                          for k in range(len(offs) - 1)])  # ~ orbital frequency: |dx|/|x|, |dv|/|v| per unit time
         bound = np.where(stopped, bound + 10.0 * np.abs(g["time"] - o["time"]) * rate, bound)
     assert np.all(dt_rel <= tbound), f"time mismatch at {np.nonzero(dt_rel > tbound)[0][:10]}: {dt_rel[dt_rel > tbound][:5]}"
-    r = np.maximum(ex, ev) / bound
+    err = np.maximum(ex, ev)
+    if sens is not None:
+        ran = o["status"] <= 1  # reached the end time: no stop on the way
+        over = err > tol
+        n_ran, n_over = int(ran.sum()), int((over & ran).sum())
+        msg = (f"strict {tol:g} bar met by {n_ran - n_over} of {n_ran} systems that ran the whole call "
+               f"({n_over} within {COND_FACTOR:g}x the oracle's own 1-ulp sensitivity, cap {max_relaxed:.0%}); "
+               f"{int((over & ~ran).sum())} of {int((~ran).sum())} stopped systems above {tol:g}")
+        print("parity:", msg)
+        assert n_over <= max_relaxed * n_ran, msg
+    r = err / bound
     worst = int(np.argmax(r))
     sw = "n/a" if sens is None else f"{sens[worst]:.3e}"
     assert r.max() <= 1.0, f"worst system {worst}: pos {ex[worst]:.3e} vel {ev[worst]:.3e} bound {bound[worst]:.3e} (sensitivity {sw})"

@@ -27,6 +27,18 @@ def test_compact_eight_body_parity_1000_steps(kind):
 
 
 @pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_wide_spaced_eight_body_parity_1000_steps(kind):
+    # planets 6 to 8 mutual Hill radii apart: most systems run the whole 1000 steps (234 of
+    # 256), and at least 90 % of those meet the strict 1e-10 bar (assert_parity's cap)
+    ens = ics.mvs_compact(256, seed=16, k_lo=6.0, k_hi=8.0)
+    o = run_oracle(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    sens = oracle_sensitivity(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    g = run_gpu(ens, 1000 * DT, kind, DT, ce=3.0, ej=100.0)
+    assert int(np.sum(o["status"] <= 1)) >= 200
+    assert_parity(ens, g, o, sens=sens)
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
 def test_ragged_mvs_parity(kind):
     ens = ics.ragged(300, seed=12)
     o = run_oracle(ens, 300 * DT, kind, DT, ce=3.0, ej=100.0)

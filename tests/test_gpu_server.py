@@ -1,10 +1,11 @@
-"""Continuous batching: requests served in a mix give the same results as alone."""
+"""Continuous batching: requests served in a mix give the same results as alone, and
+the oracle's; systems retire one by one and their slots are backfilled at once."""
 import math
 
 import numpy as np
 import pytest
 
-from gpu_util import per_system_errors
+from gpu_util import assert_parity, oracle_sensitivity, per_system_errors, run_oracle
 from paper_1208_1157_gb300 import ics
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +38,8 @@ def alone(ens, t_end, integ, ce=3.0, ej=100.0):
 
 
 def check_same(trace, ens_list, out, tol=1e-10):
+    """Each served result equals the same request run alone through an ensemble (1e-10)
+    and matches the oracle under the parity criteria of every other GPU test."""
     for r, q in enumerate(trace):
         res = out["done"][r]
         ref = alone(ens_list[r], q["t_end"], q["integrator"])
@@ -44,6 +47,11 @@ def check_same(trace, ens_list, out, tol=1e-10):
         np.testing.assert_allclose(res["time"], ref["time"], rtol=1e-13, atol=0)
         ex, ev = per_system_errors(ens_list[r], res, ref)
         assert ex.max() <= tol and ev.max() <= tol, (r, ex.max(), ev.max())
+        dt = HDT if q["integrator"] == 1 else MDT
+        kw = dict(ce=3.0, ej=100.0)
+        o = run_oracle(ens_list[r], q["t_end"], q["integrator"], dt, **kw)
+        sens = oracle_sensitivity(ens_list[r], q["t_end"], q["integrator"], dt, **kw)
+        assert_parity(ens_list[r], res, o, sens=sens, steps=int(math.ceil(q["t_end"] / dt)))
 
 
 def test_results_in_the_mix_equal_results_alone():
@@ -60,8 +68,9 @@ def test_results_in_the_mix_equal_results_alone():
 
 
 def test_backfill_when_pools_are_full():
-    # pools of 64 slots: the 5-body Hermite requests below need 150 slots in total, so the
-    # later ones wait in the queue until earlier ones retire and free their slots
+    # pools of 64 slots: the 5-body Hermite requests below need 150 slots in total; the
+    # first round fills every slot (request 0 whole, 14 systems of request 1), the rest
+    # waits in arrival order until systems retire and free their slots
     from paper_1208_1157_gb300 import server as SV
 
     trace = [{"id": r, "arrival_s": 0.0, "n_sys": 50, "n": 5, "integrator": 1, "t_end": (40 + 30 * r) * HDT,
@@ -72,7 +81,12 @@ def test_backfill_when_pools_are_full():
             sv.submit(e, q["t_end"], 1)
         sv.step()
         st = sv.stats()
-        assert st["admitted"] == 1 and st["queued"] == 2  # only one request fits at first
+        # every slot was filled; the systems that stopped within the first quantum (the
+        # oracle's count) have retired already
+        first = ics.concat(ens_list[0], ics.subset(ens_list[1], range(14)))
+        early = int(np.sum(run_oracle(first, 25 * HDT, 1, HDT, ce=3.0, ej=100.0)["status"] >= 2))
+        assert st["admitted"] == 2 and st["queued"] == 2 and st["occupied_slots"] == 64 - early
+        assert sv.poll(3)[0] == SV.REQ_QUEUED  # request 2 waits behind request 1
         out = {"done": {}}
         for _ in range(200):
             sv.step()
@@ -97,6 +111,42 @@ def test_memory_budget_releases_idle_pools():
         st = sv.stats()
     assert st["completed"] == 4 and st["device_bytes"] <= one_pool
     check_same(trace, ens_list, out)
+
+
+def test_stopped_systems_retire_at_once_and_their_slots_are_backfilled():
+    # Pool of 64 slots.  Request A: 40 systems, 12 of them with a planet placed to be
+    # ejected within the first quantum; request B: 36 systems, of which 24 fit at first.
+    # After the first round the 12 ejected systems of A retire alone, and the next round
+    # admits B's remaining 12 systems into their slots while A is still running.
+    from paper_1208_1157_gb300 import server as SV
+
+    qa = {"id": 0, "arrival_s": 0.0, "n_sys": 40, "n": 3, "integrator": 1, "t_end": 300 * HDT, "seed": 0}
+    qb = {"id": 1, "arrival_s": 0.0, "n_sys": 36, "n": 3, "integrator": 1, "t_end": 120 * HDT, "seed": 0}
+    ea = ics.three_body(40, seed=41)
+    for s in range(0, 36, 3):  # 12 systems: outer planet at 99.95 AU moving outward (past 100 AU in ~3 steps)
+        ea["pos"][3 * s + 2] = [99.95, 0.0, 0.0]
+        ea["vel"][3 * s + 2] = [3.0, 0.0, 0.0]
+    eb = ics.three_body(36, seed=42)
+    with SV.Server(slots_per_pool=64, quantum_steps=25) as sv:
+        ia, ib = sv.submit(ea, qa["t_end"], 1), sv.submit(eb, qb["t_end"], 1)
+        sv.step()  # admits A (40) and 24 of B; the ejected systems stop and retire
+        st = sv.stats()
+        assert st["occupied_slots"] == 64 - 12 and st["queued"] == 1
+        sv.step()  # B's last 12 systems take the freed slots; A is still running
+        st = sv.stats()
+        assert st["occupied_slots"] == 64 and st["queued"] == 0
+        assert sv.poll(ia)[0] == SV.REQ_RUNNING
+        out = {"done": {}}
+        for _ in range(100):
+            sv.step()
+            if sv.stats()["completed"] == 2:
+                break
+        for r, (rid, q) in enumerate(((ia, qa), (ib, qb))):
+            state, res = sv.poll(rid, q["n_sys"], q["n"])
+            assert state == SV.REQ_DONE
+            out["done"][r] = res
+    assert np.sum(out["done"][0]["status"] == 3) == 12
+    check_same([qa, qb], [ea, eb], out)
 
 
 def test_stopped_systems_retire_with_their_request():
