@@ -35,3 +35,18 @@ def test_flop_counts():
     assert f(3) == 3 * (35 * 2 + 6 + 12 + 53) + 3 * 2 * 34 + 6 == 633
     assert f(2) == 3 * (35 + 6) + 3 * 34 + 6 == 231
     assert f(4) - f(3) > f(3) - f(2)  # pairs grow quadratically
+
+
+def test_scope_table_counts():
+    # the scope table's Hermite count, 3 P 58 + 3 n 34, against its own worked figures
+    # (n = 3: ~830, n = 8: ~5.7 kflop, n = 15: ~19.8 kflop); the implemented Runge-Kutta
+    # count at n = 3 (731) and the MVS count's parts
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_counts2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    h = bench.scope_hermite_flops
+    assert h(3) == 828 and abs(h(8) - 5700) < 50 and abs(h(15) - 19800) < 50
+    assert bench.rkck_flops(3) == 731
+    assert bench.scope_mvs_flops(8, 1.0, True) == 25 * 28 + 7 * 100 + 48
+    assert bench.scope_mvs_flops(8, 2.0, False) == 25 * 21 + 7 * 130 + 48
