@@ -649,11 +649,16 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     if (m == SWARM_MAP_SYSTEM_PER_LANE && (!hermite_family(integrator) || e->bins[i].n > 4))
       m = SWARM_MAP_BODY_PER_LANE;
     maps[i] = m;
-    // MVS: one CTA of 4 warps per SM (one warp per SM sub-partition) unless set; with
-    // systems handed out per group this keeps the FP64 pipe as busy as more warps do and
-    // halves the step time of the last systems of a call (16384 x 8 compact ensemble:
-    // +4 % over 2000 steps, +35 % over 1e5 steps, where few systems run the last steps)
-    if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) bin_ctas[i] = 1;
+    // MVS calls of more than 10^4 steps: one CTA of 4 warps per SM (one warp per SM
+    // sub-partition) unless set.  Such calls end with a few long-lived systems whose step
+    // latency alone sets the time, and a second warp on their sub-partition doubles it
+    // (16384 x 8 compact ensemble over 1e5 steps: 1.31 s at one CTA per SM, 1.51 s at
+    // two); shorter calls take the tuner's choice (over 2000 steps two CTAs per SM are
+    // ahead, 1.75e8 against 1.60e8 system-steps/s, as the FP64 pipe goes from 73 to 91 %).
+    if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) {
+      const double span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
+      if (span > 1e4) bin_ctas[i] = 1;
+    }
     // adaptive system per lane: each lane integrates systems one after the other, so the
     // call ends with lanes waiting for the last ones; one CTA per SM gives every lane
     // more systems and makes that tail a smaller part of the call

@@ -22,9 +22,6 @@
 namespace swarm {
 
 namespace {
-struct Choice {
-  int32_t mapping, ctas;
-};
 std::mutex g_mu;
 std::map<std::tuple<int, int, int>, Choice> g_cache;
 
@@ -57,6 +54,10 @@ void probe_ics(int n, int S, std::vector<int32_t> &nb, std::vector<double> &m, s
   }
 }
 
+// steps of one probe launch: long enough that the launch, the first force evaluation and
+// the grid's ramp are a small part of it, so the ranking is stable from call to call
+constexpr int kProbeSteps = 64;
+
 double measure(int n, int integrator, int S, cudaStream_t st, int mapping, int ctas) {
   std::vector<int32_t> nb;
   std::vector<double> m, x, v;
@@ -66,7 +67,7 @@ double measure(int n, int integrator, int S, cudaStream_t st, int mapping, int c
   swarm_set_option(e, SWARM_OPT_MAPPING, mapping);
   if (ctas) swarm_set_option(e, SWARM_OPT_CTAS_PER_SM, ctas);
   const double dt = integrator == SWARM_HERMITE4 ? 2e-3 * M_PI : 0.1 * M_PI;
-  const int steps = 8;
+  const int steps = kProbeSteps;
   double best = 0;
   for (int rep = 0; rep < 3; rep++) {
     double t_end = (rep + 1) * steps * dt;
@@ -80,6 +81,21 @@ double measure(int n, int integrator, int S, cudaStream_t st, int mapping, int c
   return best;
 }
 }  // namespace
+
+// Candidates, in the order they are measured: body per lane at the kernel's own full
+// residency (0) and at 1, 2 and 3 CTAs of 4 warps per SM (persistent grids of 1x, 2x and
+// 3x the SM count; a count above the kernel's residency runs at its residency); for the
+// Hermite step with n <= 4 also a whole system per lane at full residency and at 1 CTA
+// per SM, and for n <= 3 its high-occupancy build (3).
+void tuner_candidates(int n, int integrator, std::vector<Choice> *out) {
+  *out = {{SWARM_MAP_BODY_PER_LANE, 0}, {SWARM_MAP_BODY_PER_LANE, 1}, {SWARM_MAP_BODY_PER_LANE, 2},
+          {SWARM_MAP_BODY_PER_LANE, 3}};
+  if (integrator == SWARM_HERMITE4 && n <= 4) {
+    out->push_back({SWARM_MAP_SYSTEM_PER_LANE, 0});
+    out->push_back({SWARM_MAP_SYSTEM_PER_LANE, 1});
+    if (n <= 3) out->push_back({SWARM_MAP_SYSTEM_PER_LANE, 3});
+  }
+}
 
 int tuner_choice_internal(int n, int integrator, int S, cudaStream_t st, int32_t *mapping, int32_t *ctas) {
   auto key = std::make_tuple(n, integrator, size_class(S));
@@ -102,12 +118,8 @@ int tuner_choice_internal(int n, int integrator, int S, cudaStream_t st, int32_t
     // probe at the bin's own size: how the work units spread over the SM sub-partitions
     // (granularity) decides between the mappings as much as the per-step cost does
     int probeS = S < (1 << 20) ? S : (1 << 20);
-    std::vector<Choice> cands = {{SWARM_MAP_BODY_PER_LANE, 0}, {SWARM_MAP_BODY_PER_LANE, 1}};
-    if (integrator == SWARM_HERMITE4 && n <= 4) {
-      cands.push_back({SWARM_MAP_SYSTEM_PER_LANE, 0});
-      // 3 CTAs per SM selects the high-occupancy build (n <= 3)
-      if (n <= 3) cands.push_back({SWARM_MAP_SYSTEM_PER_LANE, 3});
-    }
+    std::vector<Choice> cands;
+    tuner_candidates(n, integrator, &cands);
     double best = -1;
     for (auto &cd : cands) {
       double r = measure(n, integrator, probeS, st, cd.mapping, cd.ctas);
