@@ -2,6 +2,7 @@
 // two thread mappings; instantiated per body count in hermite_units_*.cu.
 #pragma once
 #include "hermite.cuh"
+#include "hermite_block.cuh"
 #include "kernels.h"
 
 namespace swarm {
@@ -1124,8 +1125,13 @@ cudaError_t launch_hermite_uniform_pick(const BinView &B, int nunits, const Step
     if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N, 2, true>();
     return grid > 0 ? launch_hermite_uniform_n<MAP, N, 2, true>(B, nunits, P, grid, st) : cudaSuccess;
   }
-  if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N>();
-  return grid > 0 ? launch_hermite_uniform_n<MAP, N>(B, nunits, P, grid, st) : cudaSuccess;
+  // fixed steps, body per lane, n >= 5: systems packed across the CTA (hermite_block.cuh)
+  if constexpr (MAP == SWARM_MAP_BODY_PER_LANE && N >= kBlockRingMinN) {
+    return launch_hermite_block_n<N>(B, nunits, P, grid, st, blocks);
+  } else {
+    if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N>();
+    return grid > 0 ? launch_hermite_uniform_n<MAP, N>(B, nunits, P, grid, st) : cudaSuccess;
+  }
 }
 
 }  // namespace swarm
