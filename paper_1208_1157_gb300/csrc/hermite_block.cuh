@@ -341,6 +341,19 @@ __global__ void __launch_bounds__(kBlockRingThreads, 2) hermite_block_kernel(Bin
   bpl_hermite_block_stream<N>(B, P, sm_block);
 }
 
+// Whether a bin (its listed systems, if it has a list) fills one wave of block-ring CTAs
+// (two per SM): below that the call is bound by the step latency of few systems.
+inline bool block_ring_pays(const BinView &B, int n) {
+  static int sms = 0;
+  if (!sms) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+      sms = 1;
+  }
+  const long long S = B.list ? B.nlist : B.S;
+  return S >= 2LL * sms * (kBlockRingThreads / n);
+}
+
 // Launch (grid > 0) and/or report the resident CTAs per SM (blocks); the kernel's
 // shared memory (up to 64 KB at n = 15) is opted into on first use.
 template <int N>

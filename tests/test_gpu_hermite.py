@@ -371,3 +371,24 @@ def test_comparable_masses_parity(integrator):
     sens = oracle_sensitivity(ens, 500 * dt, integrator, dt)
     g = run_gpu(ens, 500 * dt, integrator, dt)
     assert_parity(ens, g, o, sens=sens, steps=500)
+
+
+@pytest.mark.parametrize("ns", [(5, 8), (13, 14)])
+def test_block_ring_equals_warp_ring_bit_for_bit(ns):
+    # Bins large enough for the CTA-packed body-per-lane kernel (one wave of its CTAs),
+    # integrated by single-bin launches (packed over the CTA, shared-memory exchange) and by
+    # the shared multi-bin launch (warp ring, shuffles): the same bits, energy logs included.
+    from paper_1208_1157_gb300 import swarm as S
+
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    parts = [ics.request_ensemble({"n_sys": 2 * sms * (128 // n) + 37, "n": n, "seed": 600 + n}) for n in ns]
+    ens = ics.concat(*parts)
+    a = run_gpu(ens, 60 * DT, 1, DT, mapping=S.MAP_BODY_PER_LANE, ce=3.0, ej=100.0, single_launch=0,
+                log_interval=20, log_cap=4)
+    b = run_gpu(ens, 60 * DT, 1, DT, mapping=S.MAP_BODY_PER_LANE, ce=3.0, ej=100.0, single_launch=1,
+                log_interval=20, log_cap=4)
+    for k in ("pos", "vel", "time", "status"):
+        assert np.array_equal(a[k], b[k]), k
+    assert all(np.array_equal(x, y) for x, y in zip(a["logs"], b["logs"]))
