@@ -113,13 +113,13 @@ __device__ __forceinline__ void block_accjerk(const F64k &k, const double (&x)[3
 }
 
 // Energy (Eq. 6, pairs once) and angular momentum of the lane's system, valid in the
-// group's first lane; a CTA collective (barriers), only called at log points.
+// group's first lane; a CTA collective (barriers), only called at log points.  Shared
+// arrays: positions sx [3][T] (overwritten), masses smass [T], partial sums part [4][T].
 template <int N>
 __device__ __forceinline__ void block_energy(const double (&x)[3], const double (&v)[3], double m, int b, int gbase,
-                                             double *sm, double (&out)[4]) {
-  constexpr int T = BlockRing<N>::T;
+                                             double *sx, const double *smass, double *part, double (&out)[4]) {
+  constexpr int T = kBlockRingThreads;
   const int t = threadIdx.x;
-  double *sx = sm, *smass = sm + 6 * T, *part = sm + 8 * T;  // part: [4][T] in the slot area
 #pragma unroll
   for (int c = 0; c < 3; c++) sx[c * T + t] = x[c];
   __syncthreads();
@@ -311,7 +311,7 @@ __device__ __forceinline__ void bpl_hermite_block_stream(const BinView &B, const
       const bool need_log = alive && !code && (steps % P.log_interval) == 0;
       if (__syncthreads_or(need_log)) {
         double e4[4];
-        block_energy<N>(x, v, m, b, gbase, sm, e4);
+        block_energy<N>(x, v, m, b, gbase, sm, smass, sm + 8 * T, e4);
         if (need_log && lane_ok && b == 0) write_log(P, B.gidx[s], tt, e4);
       }
     }

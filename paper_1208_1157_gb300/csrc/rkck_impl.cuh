@@ -641,6 +641,12 @@ __device__ __forceinline__ void spl_rkck_stream(const BinView &B, const StepPara
   }
 }
 
+}  // namespace swarm
+
+#include "rkck_block.cuh"
+
+namespace swarm {
+
 // Persistent kernel for one bin: every warp streams systems through its groups until the
 // bin's counter runs out (work unit = system).
 template <int N, bool ADAPT>
@@ -653,6 +659,10 @@ __global__ void __launch_bounds__(128, 2) rkck_uniform_kernel(BinView B, int nun
 template <int N, bool ADAPT>
 cudaError_t launch_rkck_uniform_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
                                   int *blocks) {
+  // fixed steps, n >= 5, bins that fill a wave: systems packed across the CTA (rkck_block.cuh)
+  if constexpr (!ADAPT && N >= kBlockRingMinN) {
+    if (block_ring_pays(B, N)) return launch_rkck_block_n<N>(B, nunits, P, grid, st, blocks);
+  }
   if (blocks) cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, rkck_uniform_kernel<N, ADAPT>, 128, 0);
   if (grid <= 0) return cudaSuccess;
   rkck_uniform_kernel<N, ADAPT><<<grid, 128, 0, st>>>(B, nunits, P);

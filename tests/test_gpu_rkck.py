@@ -124,3 +124,24 @@ def test_rkck_fixed_backward_parity():
     sens = oracle_sensitivity(ens, t_end, O.RKCK, -DT, ce=3.0, ej=100.0)
     g = run_gpu(ens, t_end, RKCK, -DT, ce=3.0, ej=100.0)
     assert_parity(ens, g, o, sens=sens, steps=121)
+
+
+@pytest.mark.parametrize("ns", [(5, 8), (13, 14)])
+def test_block_ring_equals_warp_ring_bit_for_bit(ns):
+    # Bins large enough for the CTA-packed body-per-lane kernel (one wave of its CTAs)
+    # against 40 of their systems integrated alone (small bins: the warp ring): the same bits.
+    from paper_1208_1157_gb300 import swarm as S
+
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    parts = [ics.request_ensemble({"n_sys": 2 * sms * (128 // n) + 37, "n": n, "seed": 700 + n}) for n in ns]
+    ens = ics.concat(*parts)
+    a = run_gpu(ens, 40 * DT, S.RKCK, DT, ce=3.0, ej=100.0)
+    nb = np.asarray(ens["n_body"])
+    offs = np.concatenate([[0], np.cumsum(nb)])
+    idx = np.sort(np.random.default_rng(3).choice(len(nb), 40, replace=False))
+    b = run_gpu(ics.subset(ens, idx), 40 * DT, S.RKCK, DT, ce=3.0, ej=100.0)
+    rows = np.concatenate([np.arange(offs[s], offs[s + 1]) for s in idx])
+    assert np.array_equal(a["pos"][rows], b["pos"]) and np.array_equal(a["vel"][rows], b["vel"])
+    assert np.array_equal(a["time"][idx], b["time"]) and np.array_equal(a["status"][idx], b["status"])
