@@ -30,15 +30,20 @@ struct BinView {
   const double *t_end = nullptr;  // per-system end time (serving slots); null: the call's
   const int32_t *list = nullptr;  // systems to run (serving: the occupied slots); null: all S
   int nlist = 0;
+  const int *nlist_dev = nullptr;  // the list's length in device memory (compacted lists); null: nlist
   // the bin is the ensemble's systems g0 .. g0 + S - 1, whose caller rows start at row0
   // (every uniform ensemble); -1: its systems are scattered (gidx)
   int g0 = -1;
   long long row0 = -1;
 };
 
+// systems a launch hands out one by one
+__device__ __forceinline__ int stream_count(const BinView &B) {
+  return B.list ? (B.nlist_dev ? *B.nlist_dev : B.nlist) : B.S;
+}
 // k-th system of a launch that hands out systems one by one, or -1 past the end
 __device__ __forceinline__ int stream_system(const BinView &B, int k) {
-  if (B.list) return k < B.nlist ? B.list[k] : -1;
+  if (B.list) return k < (B.nlist_dev ? *B.nlist_dev : B.nlist) ? B.list[k] : -1;
   return k < B.S ? k : -1;
 }
 

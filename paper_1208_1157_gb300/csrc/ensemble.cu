@@ -43,6 +43,13 @@ void set_last_error(const char *msg) { g_err = msg; }
   } while (0)
 
 // ------------------------------------------------------------------ object
+// device counters: [0] the shared launch's work list, [1 + i] bin i's single-bin launch,
+// [kLiveCountBase + i] bin i's compacted list length (at most 31 bins: n = 2..32)
+constexpr int kLiveCountBase = 32;
+// MVS calls longer than this many steps run in chunks (see run_persistent)
+constexpr double kMvsChunkedSpan = 2e4;
+constexpr int kMvsChunks = 32, kMvsMinChunk = 2000;
+
 struct Bin {
   int n = 0, S = 0, S_pad = 0;
   double *x = nullptr, *v = nullptr, *m = nullptr, *t = nullptr;
@@ -378,7 +385,7 @@ extern "C" int swarm_create_ensemble(int32_t n_sys, const int32_t *n_body, const
   CKC(cudaMalloc(&e->d_stage, sizeof(double) * (7 * e->n_bodies + 5 * (size_t)n_sys)));
   CKC(cudaMalloc(&e->d_stage_status, sizeof(int32_t) * n_sys));
   CKC(cudaMalloc(&e->d_counters, sizeof(unsigned long long) * 4));
-  CKC(cudaMalloc(&e->d_work_next, sizeof(int) * 32));
+  CKC(cudaMalloc(&e->d_work_next, sizeof(int) * 2 * kLiveCountBase));
   CKC(cudaEventCreate(&e->ev0));
   CKC(cudaEventCreate(&e->ev1));
   CKC(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
@@ -742,6 +749,31 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       e->launches += 3;
     }
   }
+  // Long MVS calls run as chunks of L steps (graph-replayed), and before each chunk every
+  // MVS bin's list is compacted to its runnable systems: the stream kernel then fills only
+  // as many groups per warp as the survivors need, so once they are fewer than the warps
+  // each one runs spread over a whole warp (its step latency is what a long call waits on).
+  const bool mvs = integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI;
+  const double call_span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
+  int chunk_steps = e->steps_per_launch;
+  if (mvs && per_bin && chunk_steps <= 0 && call_span > kMvsChunkedSpan)
+    chunk_steps = std::max(kMvsMinChunk, (int)std::ceil(call_span / kMvsChunks));
+  const bool compact = mvs && chunk_steps > 0 && !uni.empty();
+  if (compact) {
+    if (!e->d_order) {
+      size_t scratch = 0;
+      for (auto &b : e->bins) scratch = std::max(scratch, order_scratch_ints(b.S));
+      CK(cudaMalloc(&e->d_order, sizeof(int32_t) * (size_t)e->n_sys));
+      CK(cudaMalloc(&e->d_order_scratch, sizeof(int) * scratch));
+    }
+    size_t off = 0;
+    for (size_t i = 0; i < uni.size(); i++) {
+      uni[i].view.list = e->d_order + off;
+      uni[i].view.nlist = uni[i].view.S;
+      uni[i].view.nlist_dev = e->d_work_next + kLiveCountBase + i;
+      off += (size_t)uni[i].view.S;
+    }
+  }
   // With more than one launch per round, the single-bin launches run on side streams
   // forked from the main stream (heaviest bin first), so that one launch's tail overlaps
   // the next launch's work; all of them join the main stream before the round ends.
@@ -765,6 +797,8 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
       StepParams Qi = Q;
       Qi.work_next = e->d_work_next + 1 + i;
       CK(cudaMemsetAsync(Qi.work_next, 0, sizeof(int), si));
+      if (compact) CK(live_list(uni[i].view, const_cast<int32_t *>(uni[i].view.list),
+                                const_cast<int *>(uni[i].view.nlist_dev), si));
       CK(launch_uni(uni[i], Qi, uni[i].grid, si, nullptr));
     }
     for (int j = 0; j < K; j++) {
@@ -773,18 +807,17 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     }
     return SWARM_OK;
   };
-  const int per_call = (int)uni.size() + (per_bin ? 0 : 1);
+  const int per_call = (int)uni.size() * (compact ? 2 : 1) + (per_bin ? 0 : 1);
   // the adaptive step count is not known in advance: always one launch per call
-  if (e->steps_per_launch <= 0 || adaptive(integrator)) {
+  if (chunk_steps <= 0 || adaptive(integrator)) {
     if ((rc = enqueue(e->stream, P))) return rc;
     e->launches += per_call;
     return SWARM_OK;
   }
   // Chunked: K rounds of launches of at most L steps each, all with identical parameters
   // (the end time is read from device memory), captured into one CUDA graph and replayed.
-  const int L = e->steps_per_launch;
-  const double span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
-  const long long nmax = (long long)std::ceil(span - 1e-9);
+  const int L = chunk_steps;
+  const long long nmax = (long long)std::ceil(call_span - 1e-9);
   const int K = (int)std::max(1LL, (nmax + L - 1) / L);
   StepParams Q = P;
   Q.max_steps = L;
@@ -794,7 +827,8 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   // every parameter the captured launches bake in
   std::vector<double> key = {2.0, (double)K, (double)L, (double)integrator, (double)grid, (double)e->nwork, P.dt,
                              (double)P.n_corr, (double)P.corr_form, P.rk_eps, P.ce_factor, P.eject2,
-                             (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)P.log, (double)per_bin};
+                             (double)P.log_interval, (double)P.log_cap, (double)(uintptr_t)P.log, (double)per_bin,
+                             (double)compact};
   for (int m : maps) key.push_back((double)m);
   for (auto &u : uni) key.push_back((double)u.grid);
   rc = replay_graph(e, key, [&](cudaStream_t cs) -> int {

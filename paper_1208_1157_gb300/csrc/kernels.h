@@ -62,6 +62,9 @@ cudaError_t launch_rkck_wide(const BinView &B, const StepParams &P, int grid, cu
 // scratch of order_scratch_ints(S) ints.
 size_t order_scratch_ints(int S);
 cudaError_t order_longest_first(const BinView &B, double t_end, int32_t *list, int *scratch, cudaStream_t st);
+// The bin's runnable systems into list, their number into *count (device): the systems a
+// chunk of a long MVS call still has to advance.
+cudaError_t live_list(const BinView &B, int32_t *list, int *count, cudaStream_t st);
 
 void set_last_error(const char *msg);
 

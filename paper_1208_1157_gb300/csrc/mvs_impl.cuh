@@ -889,12 +889,28 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
   L.plan.t_end = P.t_end;
 #pragma unroll
   for (int r = 0; r < RTA; r++) L.kc[r] = 0.0;
-  bool exhausted = false;
+  // Groups that take systems: as many per warp as the launch's systems need to be all in
+  // flight at once (at most G).  When the systems are fewer than the warps (the last
+  // chunks of a long call, compacted to the survivors), one group per warp takes systems
+  // and the others are spare from the start, so each system runs spread over its warp.
+  int ga = G;
+  {
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long need = ((long long)stream_count(B) + warps - 1) / warps;
+    if (need < G) ga = need < 1 ? 1 : (int)need;
+  }
+  bool exhausted = g >= ga;
   unsigned long long kep_iters = 0;
 
   for (;;) {
-    // ---- refill: groups without a system take the bin's next one
-    const bool need = !L.has && !exhausted;
+    // ---- refill: groups without a system take the bin's next one, as long as the warp
+    // holds fewer than ga systems (the lowest idle groups first)
+    bool need = !L.has && !exhausted;
+    {
+      const unsigned hold = __ballot_sync(FULL, L.has && lane_ok && b == 0);
+      const unsigned cand = __ballot_sync(FULL, need && lane_ok && b == 0);
+      need = need && __popc(cand & ((1u << base) - 1u)) < ga - __popc(hold);
+    }
     if (__any_sync(FULL, need)) {
       int sn = 0;
       if (need && lane_ok && b == 0) sn = atomicAdd(P.work_next, 1);
@@ -966,8 +982,7 @@ __device__ __forceinline__ void bpl_mvs_stream(const BinView &B, const StepParam
       if (2 * A <= G && __any_sync(FULL, exhausted)) {
         if (RS1 > RS2 && A * RS1 <= G) mvs_spread_run<N, JAC, RS1>(B, P, L, holders, A, g, b, lane_ok, kep_iters);
         else mvs_spread_run<N, JAC, RS2>(B, P, L, holders, A, g, b, lane_ok, kep_iters);
-        exhausted = true;
-        continue;
+        continue;  // groups without a system take the next one, if any is left
       }
     }
     // ---- one step for every group holding a system

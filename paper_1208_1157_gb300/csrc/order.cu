@@ -85,9 +85,22 @@ __global__ void order_scatter_kernel(int S, const int *__restrict__ cls, int *__
   list[atomicAdd(&start[cls[s]], 1)] = s;
 }
 
+// the bin's runnable systems (status <= DONE), in no particular order
+__global__ void live_list_kernel(BinView B, int32_t *__restrict__ list, int *__restrict__ count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B.S && B.status[s] <= SWARM_SYS_DONE) list[atomicAdd(count, 1)] = s;
+}
+
 }  // namespace
 
 size_t order_scratch_ints(int S) { return (size_t)S + 2 * kClasses; }
+
+cudaError_t live_list(const BinView &B, int32_t *list, int *count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  live_list_kernel<<<(B.S + 127) / 128, 128, 0, st>>>(B, list, count);
+  return cudaGetLastError();
+}
 
 cudaError_t order_longest_first(const BinView &B, double t_end, int32_t *list, int *scratch, cudaStream_t st) {
   int *cls = scratch, *hist = scratch + B.S, *start = hist + kClasses;

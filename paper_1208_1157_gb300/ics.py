@@ -198,8 +198,10 @@ def ragged_wide(n_sys: int, seed: int, n_min: int = 16, n_max: int = 32) -> dict
     return _assemble(n_body, 1.0, mp, a, e, inc, node, peri, E)
 
 
-def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0, k_lo: float = 3.0, k_hi: float = 8.0) -> dict:
-    """n bodies, Hill spacing as in `ragged` (K ~ U(k_lo, k_hi) mutual Hill radii), e ~ U(0, 0.1);
+def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0, k_lo: float = 3.0, k_hi: float = 8.0,
+                m_lo: float = 1e-5, m_hi: float = 1e-3) -> dict:
+    """n bodies, Hill spacing as in `ragged` (K ~ U(k_lo, k_hi) mutual Hill radii, planet
+    masses log-U(m_lo, m_hi)), e ~ U(0, 0.1);
     a system whose outermost apocentre a (1 + e) reaches `a_lim` AU is redrawn from the
     next attempt of its own stream."""
     S = n_sys
@@ -211,7 +213,7 @@ def mvs_compact(n_sys: int, seed: int, n: int = 8, a_lim: float = 50.0, k_lo: fl
         nb = n_body[todo]
         # attempt r of system s uses stream index s + r * 2^32
         idx = todo.astype(np.uint64) + np.uint64(attempt) * np.uint64(1 << 32)
-        parts = _hill_spaced(nb, seed, idx, 0.1, 1, k_lo=k_lo, k_hi=k_hi)
+        parts = _hill_spaced(nb, seed, idx, 0.1, 1, m_lo=m_lo, m_hi=m_hi, k_lo=k_lo, k_hi=k_hi)
         if out is None:
             out = [np.zeros((S,) + p.shape[1:]) for p in parts]
         apo = parts[1][:, -1] * (1.0 + parts[2][:, -1])

@@ -94,7 +94,8 @@ def test_mvs_chunked_launches(kind):
         e.set_stop(3.0, 100.0)
         e.set_option(S.OPT_STEPS_PER_LAUNCH, 50)
         e.integrate(300 * DT, kind, DT)
-        assert e.stats()["kernel_launches"] == 6
+        # six chunks, each after the launch that compacts the bin to its runnable systems
+        assert e.stats()["kernel_launches"] == 12
         got = e.state()
     from gpu_util import per_system_errors
     assert np.array_equal(got["status"], ref["status"])
@@ -144,3 +145,41 @@ def test_system_alone_equals_system_in_ensemble_bit_for_bit(kind):
         rows = slice(offs[s], offs[s + 1])
         assert a["status"][0] == g["status"][s] and a["time"][0] == g["time"][s], (s, nb[s])
         assert np.array_equal(a["pos"], g["pos"][rows]) and np.array_equal(a["vel"], g["vel"][rows]), (s, nb[s])
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_long_call_in_compacted_chunks_parity(kind):
+    # 24000 steps (> 2e4): the call runs as 12 chunks of 2000 steps, each over the systems
+    # still running, which spread over the warp's groups once they are fewer than the warps.
+    # 32 tightly packed systems (9..12 mutual Hill radii, planets of 1e-7..1e-6) stop at
+    # close encounters spread over the first chunks; 16 widely spaced ones (14..20 Hill
+    # radii, 1e-5..1e-4) run all 1200 orbits.  Over that span two round-off histories part
+    # by more than one initial 1-ulp perturbation does: each step rounds differently, and
+    # the phase error of a long orbit integration grows like steps^(3/2) u (Brouwer's law,
+    # ~4e-10 after 24000 steps), above the 1e-10 bar.  The survivors' states are held to
+    # 30x the larger of that and the oracle's own 1-ulp sensitivity, without the 10 % cap;
+    # statuses, stop times and energy errors as in every parity test.  The same call as
+    # one launch agrees to the same bound (each chunk boundary stores the state in
+    # barycentric coordinates and maps it back, a round-off perturbation of the survivors).
+    from paper_1208_1157_gb300 import swarm as S
+
+    ens = ics.concat(ics.mvs_compact(32, seed=17, k_lo=9.0, k_hi=12.0, m_lo=1e-7, m_hi=1e-6),
+                     ics.mvs_compact(16, seed=18, k_lo=14.0, k_hi=20.0, m_lo=1e-5, m_hi=1e-4))
+    T = 24000 * DT
+    o = run_oracle(ens, T, kind, DT, ce=3.0, ej=100.0)
+    sens = np.maximum(oracle_sensitivity(ens, T, kind, DT, ce=3.0, ej=100.0), 24000 ** 1.5 * 2.0 ** -53)
+    g = run_gpu(ens, T, kind, DT, ce=3.0, ej=100.0)
+    assert g["stats"]["kernel_launches"] == 2 * 12
+    stop = np.round(o["time"] / DT)
+    assert np.sum(o["status"] <= 1) >= 16 and np.sum((stop > 2000) & (stop < 24000)) >= 3
+    assert_parity(ens, g, o, sens=sens, steps=24000, max_relaxed=1.0)
+    with S.Ensemble(ens) as e:
+        e.set_stop(3.0, 100.0)
+        e.set_option(S.OPT_STEPS_PER_LAUNCH, 24000)
+        e.integrate(T, kind, DT)
+        assert e.stats()["kernel_launches"] == 2
+        one = e.state()
+    from gpu_util import per_system_errors
+    assert np.array_equal(one["status"], g["status"]) and np.array_equal(one["time"], g["time"])
+    ex, ev = per_system_errors(ens, one, g)
+    assert np.all(np.maximum(ex, ev) <= np.maximum(1e-10, 30.0 * sens))
