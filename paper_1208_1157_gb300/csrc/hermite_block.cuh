@@ -2,9 +2,11 @@
 //
 // The warp ring (ring_accjerk) holds floor(32/n) systems per warp, so for n = 9..15 a
 // fifth to a third of the lanes idle (n = 11: 22 of 32) while the FP64 pipe runs.  Here
-// the systems are packed back to back over the CTA's 128 threads (group g = threads
-// g n .. g n + n - 1, a group may span two warps): n = 11 uses 121 of 128 lanes, n = 13
-// 117, n = 14 126.  Pair data goes through shared memory instead of shuffles: each force
+// the systems are packed back to back over the CTA's threads (group g = threads
+// g n .. g n + n - 1, a group may span two warps).  The CTA has 128 or 256 threads,
+// whichever leaves fewer idle (at ~180 registers both give two warps per sub-partition,
+// as two CTAs of 128 or one of 256): n = 11 uses 253 of 256 lanes, n = 13 247, n = 14
+// 126 of 128.  Pair data goes through shared memory instead of shuffles: each force
 // evaluation writes the positions and velocities, a barrier, evaluates this lane's pairs
 // (b, b + r mod n) for the ring's rounds r and stores each pair's terms in that round's
 // slot, a barrier, then takes the reactions of the pairs (b - r, b) from their slots.
@@ -16,12 +18,15 @@
 
 namespace swarm {
 
-constexpr int kBlockRingThreads = 128;
 constexpr int kBlockRingMinN = 5;  // smaller n: the warp ring packs as well
+
+// threads per CTA for n bodies: 256 where it packs more lanes than 128 (ties: 128)
+constexpr int block_ring_threads(int n) { return (256 / n) * n > 2 * ((128 / n) * n) ? 256 : 128; }
 
 template <int N>
 struct BlockRing {
-  static constexpr int T = kBlockRingThreads;
+  static constexpr int T = block_ring_threads(N);
+  static constexpr int CPS = 256 / T;  // CTAs per SM (two warps per sub-partition)
   static constexpr int G = T / N;  // systems per CTA
   static constexpr int RF = (N - 1) / 2;
   static constexpr bool HALF = (N % 2) == 0;
@@ -118,7 +123,7 @@ __device__ __forceinline__ void block_accjerk(const F64k &k, const double (&x)[3
 template <int N>
 __device__ __forceinline__ void block_energy(const double (&x)[3], const double (&v)[3], double m, int b, int gbase,
                                              double *sx, const double *smass, double *part, double (&out)[4]) {
-  constexpr int T = kBlockRingThreads;
+  constexpr int T = BlockRing<N>::T;
   const int t = threadIdx.x;
 #pragma unroll
   for (int c = 0; c < 3; c++) sx[c * T + t] = x[c];
@@ -335,15 +340,16 @@ __device__ __forceinline__ void bpl_hermite_block_stream(const BinView &B, const
 }
 
 template <int N>
-__global__ void __launch_bounds__(kBlockRingThreads, 2) hermite_block_kernel(BinView B, int nunits, StepParams P) {
+__global__ void __launch_bounds__(BlockRing<N>::T, BlockRing<N>::CPS) hermite_block_kernel(BinView B, int nunits, StepParams P) {
   (void)nunits;
   extern __shared__ double sm_block[];
   bpl_hermite_block_stream<N>(B, P, sm_block);
 }
 
 // Whether a bin (its listed systems, if it has a list) fills one wave of block-ring CTAs
-// (two per SM): below that the call is bound by the step latency of few systems.
-inline bool block_ring_pays(const BinView &B, int n) {
+// (two warps per sub-partition): below that the call is bound by the step latency of few
+// systems.
+inline bool block_ring_pays(const BinView &B, int cps, int systems_per_cta) {
   static int sms = 0;
   if (!sms) {
     int d = 0;
@@ -351,11 +357,11 @@ inline bool block_ring_pays(const BinView &B, int n) {
       sms = 1;
   }
   const long long S = B.list ? B.nlist : B.S;
-  return S >= 2LL * sms * (kBlockRingThreads / n);
+  return S >= (long long)cps * sms * systems_per_cta;
 }
 
 // Launch (grid > 0) and/or report the resident CTAs per SM (blocks); the kernel's
-// shared memory (up to 64 KB at n = 15) is opted into on first use.
+// shared memory (up to 128 KB at n = 15) is opted into on first use.
 template <int N>
 cudaError_t launch_hermite_block_n(const BinView &B, int nunits, const StepParams &P, int grid, cudaStream_t st,
                                    int *blocks) {
@@ -368,11 +374,11 @@ cudaError_t launch_hermite_block_n(const BinView &B, int nunits, const StepParam
   }
   if (blocks) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_block_kernel<N>, kBlockRingThreads, BlockRing<N>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_block_kernel<N>, BlockRing<N>::T, BlockRing<N>::BYTES);
     *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
-  hermite_block_kernel<N><<<grid, kBlockRingThreads, BlockRing<N>::BYTES, st>>>(B, nunits, P);
+  hermite_block_kernel<N><<<grid, BlockRing<N>::T, BlockRing<N>::BYTES, st>>>(B, nunits, P);
   return cudaGetLastError();
 }
 

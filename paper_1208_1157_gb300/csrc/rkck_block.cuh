@@ -1,6 +1,7 @@
 // Runge-Kutta Cash-Karp 4(5) (Sec. 2.2.2, Sec. 4.3.3), fixed steps, body per lane packed
-// across the CTA: the acceleration-only counterpart of hermite_block.cuh.  floor(128/n)
-// systems lie back to back over the CTA's 128 threads, and each acceleration evaluation
+// across the CTA: the acceleration-only counterpart of hermite_block.cuh.  floor(T/n)
+// systems lie back to back over the CTA's T = 128 or 256 threads (the same choice as the
+// Hermite block ring), and each acceleration evaluation
 // (six per step) exchanges positions and pair terms through shared memory with two
 // barriers; the terms are accumulated in ring_acc's order with the same products, so the
 // bits are those of the warp ring.
@@ -14,8 +15,9 @@ namespace swarm {
 
 template <int N>
 struct BlockRingA {
-  static constexpr int T = kBlockRingThreads;
-  static constexpr int G = T / N;  // systems per CTA
+  static constexpr int T = block_ring_threads(N);
+  static constexpr int CPS = 256 / T;  // CTAs per SM (two warps per sub-partition)
+  static constexpr int G = T / N;      // systems per CTA
   static constexpr int RF = ARing<N>::RF;
   static constexpr int RT = ARing<N>::RT;
   // shared doubles: x [3][T], m [T], q2 [T], per round [RT][5][T]: dx, rho^3, r^2
@@ -235,7 +237,7 @@ __device__ __forceinline__ void bpl_rkck_block_stream(const BinView &B, const St
 }
 
 template <int N>
-__global__ void __launch_bounds__(kBlockRingThreads, 2) rkck_block_kernel(BinView B, int nunits, StepParams P) {
+__global__ void __launch_bounds__(BlockRingA<N>::T, BlockRingA<N>::CPS) rkck_block_kernel(BinView B, int nunits, StepParams P) {
   (void)nunits;
   extern __shared__ double sm_rkck_block[];
   bpl_rkck_block_stream<N>(B, P, sm_rkck_block);
@@ -254,11 +256,11 @@ cudaError_t launch_rkck_block_n(const BinView &B, int nunits, const StepParams &
   }
   if (blocks) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rkck_block_kernel<N>, kBlockRingThreads, BlockRingA<N>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rkck_block_kernel<N>, BlockRingA<N>::T, BlockRingA<N>::BYTES);
     *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
-  rkck_block_kernel<N><<<grid, kBlockRingThreads, BlockRingA<N>::BYTES, st>>>(B, nunits, P);
+  rkck_block_kernel<N><<<grid, BlockRingA<N>::T, BlockRingA<N>::BYTES, st>>>(B, nunits, P);
   return cudaGetLastError();
 }
 
