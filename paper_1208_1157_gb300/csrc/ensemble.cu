@@ -46,9 +46,10 @@ void set_last_error(const char *msg) { g_err = msg; }
 // device counters: [0] the shared launch's work list, [1 + i] bin i's single-bin launch,
 // [kLiveCountBase + i] bin i's compacted list length (at most 31 bins: n = 2..32)
 constexpr int kLiveCountBase = 32;
-// MVS calls longer than this many steps run in chunks (see run_persistent)
-constexpr double kMvsChunkedSpan = 2e4;
-constexpr int kMvsChunks = 32, kMvsMinChunk = 2000;
+// MVS calls longer than this many steps run in chunks of about kMvsChunkStride steps,
+// at least 2 and at most kMvsMaxChunks (see run_persistent)
+constexpr double kMvsChunkedSpan = 1500;
+constexpr int kMvsMaxChunks = 32, kMvsChunkStride = 1000;
 
 struct Bin {
   int n = 0, S = 0, S_pad = 0;
@@ -656,15 +657,16 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
     if (m == SWARM_MAP_SYSTEM_PER_LANE && (!hermite_family(integrator) || e->bins[i].n > 4))
       m = SWARM_MAP_BODY_PER_LANE;
     maps[i] = m;
-    // MVS calls of more than 10^4 steps: one CTA of 4 warps per SM (one warp per SM
+    // MVS calls of 5000 steps or more: one CTA of 4 warps per SM (one warp per SM
     // sub-partition) unless set.  Such calls end with a few long-lived systems whose step
     // latency alone sets the time, and a second warp on their sub-partition doubles it
-    // (16384 x 8 compact ensemble over 1e5 steps: 1.31 s at one CTA per SM, 1.51 s at
-    // two); shorter calls take the tuner's choice (over 2000 steps two CTAs per SM are
-    // ahead, 1.75e8 against 1.60e8 system-steps/s, as the FP64 pipe goes from 73 to 91 %).
+    // (16384 x 8 compact ensemble, chunked calls: 1e4 steps 189 ms at one CTA per SM, 213
+    // at two; 1e5 steps 1.18 s against 1.79 s; 5000 steps even); shorter calls take the
+    // tuner's choice (over 2000 steps 2-3 CTAs per SM are ahead, 1.88e8 against 1.64e8
+    // system-steps/s, as the FP64 pipe goes from 73 to 91 %).
     if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) {
       const double span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
-      if (span > 1e4) bin_ctas[i] = 1;
+      if (span >= 5000) bin_ctas[i] = 1;
     }
     // adaptive system per lane: each lane integrates systems one after the other, so the
     // call ends with lanes waiting for the last ones; one CTA per SM gives every lane
@@ -751,13 +753,17 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   }
   // Long MVS calls run as chunks of L steps (graph-replayed), and before each chunk every
   // MVS bin's list is compacted to its runnable systems: the stream kernel then fills only
-  // as many groups per warp as the survivors need, so once they are fewer than the warps
-  // each one runs spread over a whole warp (its step latency is what a long call waits on).
+  // as many groups per warp as the survivors need: the survivors start every chunk spread
+  // evenly over the warps, and once they are fewer than the warps each one runs spread
+  // over a whole warp (its step latency is what a long call waits on).  16384 x 8 compact
+  // ensemble: 2000 steps 1.74e8 -> 1.87e8 system-steps/s, 1e5 steps 1.32 -> 1.18 s.
   const bool mvs = integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI;
   const double call_span = std::max(std::fabs(P.t_end - e->t_lo), std::fabs(P.t_end - e->t_hi)) / std::fabs(P.dt);
   int chunk_steps = e->steps_per_launch;
-  if (mvs && per_bin && chunk_steps <= 0 && call_span > kMvsChunkedSpan)
-    chunk_steps = std::max(kMvsMinChunk, (int)std::ceil(call_span / kMvsChunks));
+  if (mvs && per_bin && chunk_steps <= 0 && call_span > kMvsChunkedSpan) {
+    const double chunks = std::min((double)kMvsMaxChunks, std::max(2.0, std::floor(call_span / kMvsChunkStride)));
+    chunk_steps = (int)std::ceil(call_span / chunks);
+  }
   const bool compact = mvs && chunk_steps > 0 && !uni.empty();
   if (compact) {
     if (!e->d_order) {
