@@ -373,6 +373,7 @@ def secondary(S, torch, stream, peak):
     c3 = ics.ragged(65536, seed=3)
     out["c3_ragged_hermite_per_bin_launches_1e4_steps"] = timed_per_bin(S, stream, c3, 1e4 * DT, DT, peak)
     out["c3_ragged_hermite_single_launch_1e4_steps"] = timed_per_bin(S, stream, c3, 1e4 * DT, DT, peak, single=1)
+    out["c3_ragged_hermite_bins_alone_500_steps"] = bins_alone(S, stream, c3, 500, DT, peak)
     c4 = ics.mvs_compact(16384, seed=4)
     out["c4_mvs_jacobi_2000_steps"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20)
     out["c4_mvs_jacobi_2000_steps_2cta"] = timed(c4, 2000 * TWO_PI / 20, S.MVS_JACOBI, TWO_PI / 20, ctas=2)
@@ -423,6 +424,24 @@ def timed_per_bin(S, stream, ens, t_end, dt, peak, single=0):
             "kepler_iterations": 0, "fp64_flops": flops, "fp64_tflops": flops / sec / 1e12, "fp64_frac": flops / sec / peak,
             "fp64_count": "scope table: 3 P 58 + 3 n 34 per Hermite step",
             "fp64_flops_share_by_n": {n: f / flops for n, f in per_n.items()}}
+
+
+def bins_alone(S, stream, ens, steps, dt, peak):
+    """Each body count's systems integrated by themselves (one single-bin launch, `steps`
+    fixed steps): system-steps/s and FP64 fraction per n by the scope table's count.  A
+    bin alone runs in whole waves of its groups, which the concurrent launches hide."""
+    import numpy as np
+
+    from paper_1208_1157_gb300 import ics
+
+    nb = np.asarray(ens["n_body"])
+    out = {}
+    for n in np.unique(nb):
+        sub = ics.subset(ens, np.flatnonzero(nb == n))
+        r = timed_per_bin(S, stream, sub, steps * dt, dt, peak)
+        out[int(n)] = {"systems": int(np.sum(nb == n)), "system_steps_per_s": r["system_steps_per_s"],
+                       "fp64_frac": r["fp64_frac"]}
+    return out
 
 
 def served_flops(trace, results):

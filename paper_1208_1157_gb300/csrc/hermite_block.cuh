@@ -26,7 +26,9 @@ constexpr int block_ring_threads(int n) { return (256 / n) * n > 2 * ((128 / n) 
 template <int N>
 struct BlockRing {
   static constexpr int T = block_ring_threads(N);
-  static constexpr int CPS = 256 / T;  // CTAs per SM (two warps per sub-partition)
+  // CTAs per SM: two warps per sub-partition (one CTA of 256 or two of 128), three of 128
+  // for n <= 9, whose kernels fit 170 registers
+  static constexpr int CPS = T == 256 ? 1 : (N <= 9 ? 3 : 2);
   static constexpr int G = T / N;  // systems per CTA
   static constexpr int RF = (N - 1) / 2;
   static constexpr bool HALF = (N % 2) == 0;
@@ -349,15 +351,30 @@ __global__ void __launch_bounds__(BlockRing<N>::T, BlockRing<N>::CPS) hermite_bl
 // Whether a bin (its listed systems, if it has a list) fills one wave of block-ring CTAs
 // (two warps per sub-partition): below that the call is bound by the step latency of few
 // systems.
-inline bool block_ring_pays(const BinView &B, int cps, int systems_per_cta) {
+inline int block_ring_sms() {
   static int sms = 0;
   if (!sms) {
     int d = 0;
     if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
       sms = 1;
   }
+  return sms;
+}
+
+inline bool block_ring_pays(const BinView &B, int cps, int systems_per_cta) {
   const long long S = B.list ? B.nlist : B.S;
-  return S >= (long long)cps * sms * systems_per_cta;
+  return S >= (long long)cps * block_ring_sms() * systems_per_cta;
+}
+
+// Resident CTAs per SM to report for a block-ring launch: a third 128-thread CTA (n <= 9)
+// only where it takes the bin in fewer waves of groups than two do; in steady state the
+// third warp per sub-partition gains nothing (the FP64 pipe is already ~92 % busy) and
+// adds barrier waits.
+inline int block_ring_ctas(const BinView &B, int resident, int systems_per_cta) {
+  if (resident <= 2) return resident;
+  const long long S = B.list ? B.nlist : B.S;
+  const long long per2 = 2LL * block_ring_sms() * systems_per_cta, per3 = per2 / 2 * 3;
+  return (S + per3 - 1) / per3 < (S + per2 - 1) / per2 ? 3 : 2;
 }
 
 // Launch (grid > 0) and/or report the resident CTAs per SM (blocks); the kernel's
@@ -375,7 +392,7 @@ cudaError_t launch_hermite_block_n(const BinView &B, int nunits, const StepParam
   if (blocks) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_block_kernel<N>, BlockRing<N>::T, BlockRing<N>::BYTES);
-    *blocks = nb;
+    *blocks = block_ring_ctas(B, nb, BlockRing<N>::G);
   }
   if (grid <= 0) return cudaSuccess;
   hermite_block_kernel<N><<<grid, BlockRing<N>::T, BlockRing<N>::BYTES, st>>>(B, nunits, P);
