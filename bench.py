@@ -733,9 +733,9 @@ def ncu_case(name):
         ens = ics.mvs_compact(16384, seed=4)
         mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 200, S.MVS_JACOBI, TWO_PI / 20
         ctas = 2 if name == "mvs_2cta" else 0
-    elif name == "ragged":
+    elif name == "ragged":  # the 65536-system ragged ensemble as the benchmark runs it, 200 steps
         ens = ics.ragged(65536, seed=3)
-        mapping, steps, integ, dt = S.MAP_BODY_PER_LANE, 2, S.HERMITE4, DT
+        mapping, steps, integ, dt = S.MAP_AUTO, 200, S.HERMITE4, DT
     elif name.startswith("ragged_bin"):  # one body count of the ragged set (default n = 13), 100 steps
         import numpy as np
 

@@ -26,9 +26,7 @@ constexpr int block_ring_threads(int n) { return (256 / n) * n > 2 * ((128 / n) 
 template <int N>
 struct BlockRing {
   static constexpr int T = block_ring_threads(N);
-  // CTAs per SM: two warps per sub-partition (one CTA of 256 or two of 128), three of 128
-  // for n <= 9, whose kernels fit 170 registers
-  static constexpr int CPS = T == 256 ? 1 : (N <= 9 ? 3 : 2);
+  static constexpr int CPS = 256 / T;  // CTAs per SM (two warps per sub-partition)
   static constexpr int G = T / N;  // systems per CTA
   static constexpr int RF = (N - 1) / 2;
   static constexpr bool HALF = (N % 2) == 0;
@@ -361,21 +359,13 @@ inline int block_ring_sms() {
   return sms;
 }
 
-inline bool block_ring_pays(const BinView &B, int cps, int systems_per_cta) {
+// (n dividing 32 never: the warp ring already uses every lane, without barriers.)
+inline bool block_ring_pays(const BinView &B, int n, int cps, int systems_per_cta) {
+  if (32 % n == 0) return false;
   const long long S = B.list ? B.nlist : B.S;
   return S >= (long long)cps * block_ring_sms() * systems_per_cta;
 }
 
-// Resident CTAs per SM to report for a block-ring launch: a third 128-thread CTA (n <= 9)
-// only where it takes the bin in fewer waves of groups than two do; in steady state the
-// third warp per sub-partition gains nothing (the FP64 pipe is already ~92 % busy) and
-// adds barrier waits.
-inline int block_ring_ctas(const BinView &B, int resident, int systems_per_cta) {
-  if (resident <= 2) return resident;
-  const long long S = B.list ? B.nlist : B.S;
-  const long long per2 = 2LL * block_ring_sms() * systems_per_cta, per3 = per2 / 2 * 3;
-  return (S + per3 - 1) / per3 < (S + per2 - 1) / per2 ? 3 : 2;
-}
 
 // Launch (grid > 0) and/or report the resident CTAs per SM (blocks); the kernel's
 // shared memory (up to 128 KB at n = 15) is opted into on first use.
@@ -392,7 +382,7 @@ cudaError_t launch_hermite_block_n(const BinView &B, int nunits, const StepParam
   if (blocks) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hermite_block_kernel<N>, BlockRing<N>::T, BlockRing<N>::BYTES);
-    *blocks = block_ring_ctas(B, nb, BlockRing<N>::G);
+    *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
   hermite_block_kernel<N><<<grid, BlockRing<N>::T, BlockRing<N>::BYTES, st>>>(B, nunits, P);

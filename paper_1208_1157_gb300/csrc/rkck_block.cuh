@@ -16,7 +16,7 @@ namespace swarm {
 template <int N>
 struct BlockRingA {
   static constexpr int T = block_ring_threads(N);
-  static constexpr int CPS = T == 256 ? 1 : (N <= 9 ? 3 : 2);  // CTAs per SM, as the Hermite block ring
+  static constexpr int CPS = 256 / T;  // CTAs per SM (two warps per sub-partition)
   static constexpr int G = T / N;      // systems per CTA
   static constexpr int RF = ARing<N>::RF;
   static constexpr int RT = ARing<N>::RT;
@@ -257,7 +257,7 @@ cudaError_t launch_rkck_block_n(const BinView &B, int nunits, const StepParams &
   if (blocks) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rkck_block_kernel<N>, BlockRingA<N>::T, BlockRingA<N>::BYTES);
-    *blocks = block_ring_ctas(B, nb, BlockRingA<N>::G);
+    *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
   rkck_block_kernel<N><<<grid, BlockRingA<N>::T, BlockRingA<N>::BYTES, st>>>(B, nunits, P);

@@ -143,3 +143,12 @@ def assert_parity(ens, g, o, tol=TOL, check_energy=True, sens=None, steps=1000, 
         bad = dg > np.maximum(2 * do, steps * U)
         assert not bad.any(), f"energy error above 2x the oracle's at {np.nonzero(bad)[0][:10]}: {dg[bad][:5]} vs {do[bad][:5]}"
     return ex, ev
+
+
+def block_ring_wave(n, sms):
+    """Systems in one wave of the CTA-packed body-per-lane kernels (hermite_block.cuh,
+    rkck_block.cuh): 256-thread CTAs, one per SM, where they pack more lanes than 128,
+    else two CTAs of 128 per SM; floor(T / n) systems per CTA.  Bins of at least this
+    many systems of n bodies (n not dividing 32) take those kernels."""
+    T = 256 if (256 // n) * n > 2 * ((128 // n) * n) else 128
+    return (256 // T) * sms * (T // n)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_util import TWO_PI, assert_parity, oracle_sensitivity, per_system_errors, run_gpu, run_oracle
+from gpu_util import TWO_PI, assert_parity, block_ring_wave, oracle_sensitivity, per_system_errors, run_gpu, run_oracle
 from paper_1208_1157_gb300 import ics
 
 pytestmark = pytest.mark.gpu
@@ -373,7 +373,7 @@ def test_comparable_masses_parity(integrator):
     assert_parity(ens, g, o, sens=sens, steps=500)
 
 
-@pytest.mark.parametrize("ns", [(5, 8), (13, 14)])
+@pytest.mark.parametrize("ns", [(5, 9), (13, 14)])
 def test_block_ring_equals_warp_ring_bit_for_bit(ns):
     # Bins large enough for the CTA-packed body-per-lane kernel (one wave of its CTAs),
     # integrated by single-bin launches (packed over the CTA, shared-memory exchange) and by
@@ -383,7 +383,7 @@ def test_block_ring_equals_warp_ring_bit_for_bit(ns):
     import torch
 
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    parts = [ics.request_ensemble({"n_sys": 2 * sms * (128 // n) + 37, "n": n, "seed": 600 + n}) for n in ns]
+    parts = [ics.request_ensemble({"n_sys": block_ring_wave(n, sms) + 37, "n": n, "seed": 600 + n}) for n in ns]
     ens = ics.concat(*parts)
     a = run_gpu(ens, 60 * DT, 1, DT, mapping=S.MAP_BODY_PER_LANE, ce=3.0, ej=100.0, single_launch=0,
                 log_interval=20, log_cap=4)

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_util import TWO_PI, assert_parity, oracle_sensitivity, per_system_errors, run_gpu, run_oracle
+from gpu_util import TWO_PI, assert_parity, block_ring_wave, oracle_sensitivity, per_system_errors, run_gpu, run_oracle
 from paper_1208_1157_gb300 import ics
 
 pytestmark = pytest.mark.gpu
@@ -126,7 +126,7 @@ def test_rkck_fixed_backward_parity():
     assert_parity(ens, g, o, sens=sens, steps=121)
 
 
-@pytest.mark.parametrize("ns", [(5, 8), (13, 14)])
+@pytest.mark.parametrize("ns", [(5, 9), (13, 14)])
 def test_block_ring_equals_warp_ring_bit_for_bit(ns):
     # Bins large enough for the CTA-packed body-per-lane kernel (one wave of its CTAs)
     # against 40 of their systems integrated alone (small bins: the warp ring): the same bits.
@@ -135,7 +135,7 @@ def test_block_ring_equals_warp_ring_bit_for_bit(ns):
     import torch
 
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    parts = [ics.request_ensemble({"n_sys": 2 * sms * (128 // n) + 37, "n": n, "seed": 700 + n}) for n in ns]
+    parts = [ics.request_ensemble({"n_sys": block_ring_wave(n, sms) + 37, "n": n, "seed": 700 + n}) for n in ns]
     ens = ics.concat(*parts)
     a = run_gpu(ens, 40 * DT, S.RKCK, DT, ce=3.0, ej=100.0)
     nb = np.asarray(ens["n_body"])
