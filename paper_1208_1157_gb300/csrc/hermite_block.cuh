@@ -346,9 +346,6 @@ __global__ void __launch_bounds__(BlockRing<N>::T, BlockRing<N>::CPS) hermite_bl
   bpl_hermite_block_stream<N>(B, P, sm_block);
 }
 
-// Whether a bin (its listed systems, if it has a list) fills one wave of block-ring CTAs
-// (two warps per sub-partition): below that the call is bound by the step latency of few
-// systems.
 inline int block_ring_sms() {
   static int sms = 0;
   if (!sms) {
@@ -359,11 +356,25 @@ inline int block_ring_sms() {
   return sms;
 }
 
-// (n dividing 32 never: the warp ring already uses every lane, without barriers.)
-inline bool block_ring_pays(const BinView &B, int n, int cps, int systems_per_cta) {
+// Whether a bin of n-body systems (its listed systems, if it has a list) runs faster packed
+// over the CTA (T threads, cps CTAs per SM) than on the warp ring (floor(32/n) systems per
+// warp, two CTAs of four warps per SM).  Both hand systems out per group, so a bin takes
+// whole waves of its groups; measured on the ~5000-system bins of the ragged ensemble
+// (500 steps alone, FP64 fraction warp / block ring): n = 5 0.45 / 0.43, 6 0.48 / 0.48,
+// 7 0.42 / 0.63, 9 0.51 / 0.54, 10 0.54 / 0.42, 11 0.37 / 0.51, 13 0.45 / 0.58,
+// 15 0.53 / 0.69.  Hence: the block ring when it takes the bin in fewer waves, or in as
+// many with at least 10 % more lanes busy (its barriers cost a few per cent); never for n
+// dividing 32 (the warp ring uses every lane) nor for bins under 3/4 of its wave (bound by
+// the step latency of few systems, where the warp ring's shuffles are shorter).
+inline bool block_ring_pays(const BinView &B, int n, int T, int cps) {
   if (32 % n == 0) return false;
   const long long S = B.list ? B.nlist : B.S;
-  return S >= (long long)cps * block_ring_sms() * systems_per_cta;
+  const long long sms = block_ring_sms();
+  const long long gb = (long long)cps * sms * (T / n), gw = 8LL * sms * (32 / n);  // groups per wave
+  if (4 * S < 3 * gb) return false;
+  const long long wb = (S + gb - 1) / gb, ww = (S + gw - 1) / gw;
+  if (wb != ww) return wb < ww;
+  return 10LL * (T / n) * 32 >= 11LL * (32 / n) * T;  // lanes busy: (T/n) n / T against (32/n) n / 32
 }
 
 

@@ -149,6 +149,8 @@ def block_ring_wave(n, sms):
     """Systems in one wave of the CTA-packed body-per-lane kernels (hermite_block.cuh,
     rkck_block.cuh): 256-thread CTAs, one per SM, where they pack more lanes than 128,
     else two CTAs of 128 per SM; floor(T / n) systems per CTA.  Bins of at least this
-    many systems of n bodies (n not dividing 32) take those kernels."""
+    many systems of n bodies take those kernels when the warp ring (floor(32/n) systems
+    per warp, 8 warps per SM) needs more waves or as many with 10 % fewer lanes busy
+    (n = 7, 9, 11..15 here)."""
     T = 256 if (256 // n) * n > 2 * ((128 // n) * n) else 128
     return (256 // T) * sms * (T // n)

@@ -373,7 +373,7 @@ def test_comparable_masses_parity(integrator):
     assert_parity(ens, g, o, sens=sens, steps=500)
 
 
-@pytest.mark.parametrize("ns", [(5, 9), (13, 14)])
+@pytest.mark.parametrize("ns", [(7, 9), (13, 14)])
 def test_block_ring_equals_warp_ring_bit_for_bit(ns):
     # Bins large enough for the CTA-packed body-per-lane kernel (one wave of its CTAs),
     # integrated by single-bin launches (packed over the CTA, shared-memory exchange) and by
