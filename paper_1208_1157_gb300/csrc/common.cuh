@@ -76,6 +76,7 @@ struct StepParams {
   const double *t_end_dev = nullptr;  // end time read from device memory (graph replays)
   double rk_eps = 1e-12;  // error tolerance of the adaptive Runge-Kutta Cash-Karp step
   F64k fk = {0.0, -1.0, 1.0};  // opaque constants (set on the host, never changed)
+  int concurrent = 0;          // host-side hint: other bins' launches overlap this one
 };
 
 __device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -92,10 +93,11 @@ __device__ __forceinline__ bool nonneg_lt(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
-// 1/d for a positive normal d, to a few ulp: the approximate reciprocal of the hardware
-// (rcp.approx.ftz.f64) refined by one Newton-Raphson step r' = r + r (1 - d r), which
-// squares its relative error.  For Newton corrections, whose own accuracy only has to
-// beat the remaining error of the iteration by a wide margin, not for results.
+// 1/d for a positive normal d to ~1e-12 relative: the approximate reciprocal of the
+// hardware (rcp.approx.ftz.f64, ~1e-6) refined by one Newton-Raphson step
+// r' = r + r (1 - d r), which squares its relative error.  For Newton corrections, whose
+// own accuracy only has to beat the remaining error of the iteration by a wide margin,
+// not for results.
 __device__ __forceinline__ double rcp_newton(const F64k &k, double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));

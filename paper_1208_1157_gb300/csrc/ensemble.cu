@@ -632,7 +632,8 @@ static bool adaptive(int integrator) {
   return integrator == SWARM_HERMITE4_ADAPTIVE || integrator == SWARM_RKCK_ADAPTIVE;
 }
 
-static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator) {
+static int run_persistent(swarm_ensemble *e, const StepParams &P0, int integrator) {
+  StepParams P = P0;
   std::vector<int> maps(e->bins.size()), bin_ctas(e->bins.size(), e->ctas_per_sm);
   int ctas = e->ctas_per_sm;
   for (size_t i = 0; i < e->bins.size(); i++) {
@@ -681,6 +682,9 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P, int integrator
   // one launch over every bin (the cost-ordered work list), or one single-bin kernel per bin
   // (body inlined, registers sized for that n) when there is one bin or the option asks
   const bool per_bin = e->bins.size() - wide.size() <= 1 || !e->single_launch || rkck_family(integrator);
+  // single-bin launches that overlap one another (the kernel choice may differ from a
+  // bin launched alone, whose partly filled last wave nothing else fills)
+  P.concurrent = e->bins.size() > 1 ? 1 : 0;
   const int sms = sm_count();
   struct Uni {
     BinView view;

@@ -365,16 +365,21 @@ inline int block_ring_sms() {
 // 15 0.53 / 0.69.  Hence: the block ring when it takes the bin in fewer waves, or in as
 // many with at least 10 % more lanes busy (its barriers cost a few per cent); never for n
 // dividing 32 (the warp ring uses every lane) nor for bins under 3/4 of its wave (bound by
-// the step latency of few systems, where the warp ring's shuffles are shorter).
-inline bool block_ring_pays(const BinView &B, int n, int T, int cps) {
+// the step latency of few systems, where the warp ring's shuffles are shorter).  When
+// other bins' launches overlap this one (concurrent), they fill its last wave, and more
+// busy lanes decide alone (the 65536-system ragged call over 10^4 steps: 9.92e7 with the
+// wave rule, 1.00e8 system-steps/s with this one, n = 10 moving to the block ring).
+inline bool block_ring_pays(const BinView &B, int n, int T, int cps, bool concurrent) {
   if (32 % n == 0) return false;
   const long long S = B.list ? B.nlist : B.S;
   const long long sms = block_ring_sms();
   const long long gb = (long long)cps * sms * (T / n), gw = 8LL * sms * (32 / n);  // groups per wave
   if (4 * S < 3 * gb) return false;
+  const long long lb = (long long)(T / n) * 32, lw = (long long)(32 / n) * T;  // busy lanes, scaled
+  if (concurrent) return lb > lw;
   const long long wb = (S + gb - 1) / gb, ww = (S + gw - 1) / gw;
   if (wb != ww) return wb < ww;
-  return 10LL * (T / n) * 32 >= 11LL * (32 / n) * T;  // lanes busy: (T/n) n / T against (32/n) n / 32
+  return 10 * lb >= 11 * lw;
 }
 
 

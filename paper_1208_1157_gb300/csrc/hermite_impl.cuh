@@ -1129,7 +1129,7 @@ cudaError_t launch_hermite_uniform_pick(const BinView &B, int nunits, const Step
   // when the bin fills a wave of those CTAs; a smaller bin's step latency is the limit,
   // and the warp ring's shuffles are shorter than the block ring's barriers there
   if constexpr (MAP == SWARM_MAP_BODY_PER_LANE && N >= kBlockRingMinN) {
-    if (block_ring_pays(B, N, BlockRing<N>::T, BlockRing<N>::CPS)) return launch_hermite_block_n<N>(B, nunits, P, grid, st, blocks);
+    if (block_ring_pays(B, N, BlockRing<N>::T, BlockRing<N>::CPS, P.concurrent != 0)) return launch_hermite_block_n<N>(B, nunits, P, grid, st, blocks);
   }
   if (blocks) *blocks = hermite_uniform_blocks_n<MAP, N>();
   return grid > 0 ? launch_hermite_uniform_n<MAP, N>(B, nunits, P, grid, st) : cudaSuccess;

@@ -661,7 +661,7 @@ cudaError_t launch_rkck_uniform_n(const BinView &B, int nunits, const StepParams
                                   int *blocks) {
   // fixed steps, n >= 5, bins that fill a wave: systems packed across the CTA (rkck_block.cuh)
   if constexpr (!ADAPT && N >= kBlockRingMinN) {
-    if (block_ring_pays(B, N, BlockRingA<N>::T, BlockRingA<N>::CPS)) return launch_rkck_block_n<N>(B, nunits, P, grid, st, blocks);
+    if (block_ring_pays(B, N, BlockRingA<N>::T, BlockRingA<N>::CPS, P.concurrent != 0)) return launch_rkck_block_n<N>(B, nunits, P, grid, st, blocks);
   }
   if (blocks) cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, rkck_uniform_kernel<N, ADAPT>, 128, 0);
   if (grid <= 0) return cudaSuccess;
