@@ -95,7 +95,9 @@ enum swarm_option {
                                     integrators choose their own (system per lane for n <= 3,
                                     body per lane above) */
   SWARM_OPT_N_CORR = 2,         /* Hermite corrector passes, 1..8 (default 2, Sec. 2.2.1) */
-  SWARM_OPT_LOG_INTERVAL = 3,   /* steps between energy/angular-momentum records, 0 = off */
+  SWARM_OPT_LOG_INTERVAL = 3,   /* steps between energy/angular-momentum records, 0 = off;
+                                    counted from the call's start (with
+                                    SWARM_OPT_STEPS_PER_LAUNCH set: from each launch's start) */
   SWARM_OPT_LOG_CAPACITY = 4,   /* records kept per system (ring of this size), 0..65536 */
   SWARM_OPT_STEPS_PER_LAUNCH = 5,/* 0 = whole call in one persistent launch; else launches of
                                     this many steps, replayed from a captured CUDA graph */

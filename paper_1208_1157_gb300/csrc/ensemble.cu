@@ -767,6 +767,10 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P0, int integrato
   if (mvs && per_bin && chunk_steps <= 0 && call_span > kMvsChunkedSpan) {
     const double chunks = std::min((double)kMvsMaxChunks, std::max(2.0, std::floor(call_span / kMvsChunkStride)));
     chunk_steps = (int)std::ceil(call_span / chunks);
+    // log records fall every log_interval steps of a launch: whole intervals per chunk
+    // keep them where the call as one launch puts them
+    if (P.log_interval > 0)
+      chunk_steps = (int)std::min(2e9, std::ceil((double)chunk_steps / P.log_interval) * P.log_interval);
   }
   const bool compact = mvs && chunk_steps > 0 && !uni.empty();
   if (compact) {

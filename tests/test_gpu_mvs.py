@@ -218,3 +218,20 @@ def test_compacted_chunks_skip_stopped_systems_bit_for_bit(kind):
         assert np.array_equal(a["pos"][so[i]:so[i + 1]], g["pos"][offs[s]:offs[s + 1]]), s
         assert np.array_equal(a["vel"][so[i]:so[i + 1]], g["vel"][offs[s]:offs[s + 1]]), s
     assert np.sum(a["status"] >= 2) > 0 and np.sum(a["status"] == 1) > 0  # stops on the way, and survivors
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_chunked_call_keeps_log_records_in_place(kind):
+    # 2500 steps with a record every 1000: the call is split into chunks of whole log
+    # intervals (2000 and 500 steps here, not two of 1250), so the records fall at steps
+    # 1000 and 2000 as in the oracle
+    ens = ics.mvs_compact(24, seed=18, k_lo=14.0, k_hi=20.0, m_lo=1e-5, m_hi=1e-4)
+    T = 2500 * DT
+    o = run_oracle(ens, T, kind, DT, ce=3.0, ej=100.0, log_interval=1000, log_cap=4)
+    g = run_gpu(ens, T, kind, DT, ce=3.0, ej=100.0, log_interval=1000, log_cap=4)
+    assert g["stats"]["kernel_launches"] == 2 * 2
+    for s in range(len(ens["n_body"])):
+        lg = g["logs"][s]
+        assert len(lg) == o["log_count"][s] == 2
+        np.testing.assert_allclose(lg[:, 0], o["log"][s, :2, 0], rtol=1e-14)
+        np.testing.assert_allclose(lg[:, 1:], o["log"][s, :2, 1:], rtol=1e-9, atol=1e-14)
