@@ -185,7 +185,9 @@ def build_kepler(d):
     mvs = open(SRC).read()
     stumpff = re.search(r"__device__ __forceinline__ void stumpff23\(double z, double &c2, double &c3\) \{.*?\n\}\n",
                         mvs, re.S).group(0)
-    kep = mvs[mvs.index("struct KepConst {"):mvs.index("// ---------------------------------------------------------------- coordinate maps")]
+    # up to the replica-shared form of the drift (warp shuffles; its bits are the plain
+    # drift's, checked on the GPU against a system integrated alone)
+    kep = mvs[mvs.index("struct KepConst {"):mvs.index("// ---------------------------------------------------------------- drift shared by replicas")]
     prog = HOST_SHIMS + "namespace swarm {\n" + common_helpers() + stumpff + kep + "}\n" + KEPLER_MAIN
     with open(os.path.join(d, "k.cpp"), "w") as f:
         f.write(prog)
