@@ -398,6 +398,7 @@ def secondary(S, torch, stream, peak):
     out["wide_16_to_32_bodies_rkck_20_steps"] = timed(c6, 20 * DT, S.RKCK, DT)
     out["serving"] = serving(S, stream, peak)
     out["serving_vs_plain_hermite_n3_8_t_end_divided_by_1000"] = serving_vs_plain(S, stream, peak)
+    out["serving_by_integrator_t_end_divided_by_1000"] = serving_by_integrator(S, stream, peak)
     return out
 
 
@@ -496,6 +497,34 @@ def serving(S, stream, peak, n_req=512, rate=200.0, scales=((2000.0, 16384), (10
             "fp64_frac_of_kernel_time": flops / (kms * 1e-3) / peak,
             "fp64_count": "scope table (Hermite; MVS-DH at one Newton iteration per drift)"}
     return res
+
+
+def serving_by_integrator(S, stream, peak, F=1000.0, quantum=200):
+    """Attribution of the served FP64 fraction: the t_end / F trace split into its Hermite
+    and its MVS-DH requests, each half served alone with all its requests present at the
+    start (closed loop), FP64 work by the scope table's counts over kernel time.  The mix
+    lands between the two halves, weighted by their kernel time."""
+    from paper_1208_1157_gb300 import ics
+    from paper_1208_1157_gb300 import server as SV
+
+    full = ics.serving_trace(n_req=512, seed=5, rate=200.0, t_scale=F)
+    out = {}
+    for name, integ in (("hermite", 1), ("mvs_dh", 2)):
+        trace = [dict(q, arrival_s=0.0) for q in full if q["integrator"] == integ]
+        ens = [ics.request_ensemble(q) for q in trace]
+        with SV.Server(slots_per_pool=16384, quantum_steps=quantum, stream=stream) as sv:
+            warm = [dict(q, t_end=q["t_end"] * 1e-3) for q in trace[:16]]
+            SV.replay(sv, warm, ens[:16])
+            base = sv.stats()
+            r = SV.replay(sv, trace, ens, collect=True)
+            st = sv.stats()
+        steps = st["system_steps"] - base["system_steps"]
+        kms = st["kernel_ms"] - base["kernel_ms"]
+        flops = served_flops(trace, r["done"])
+        out[name] = {"requests": len(trace), "system_steps": steps, "kernel_ms": kms, "wall_s": r["wall_s"],
+                     "system_steps_per_s_kernel": steps / (kms * 1e-3), "fp64_flops": flops,
+                     "fp64_frac_of_kernel_time": flops / (kms * 1e-3) / peak}
+    return out
 
 
 def serving_vs_plain(S, stream, peak, F=1000.0, quantum=200):
