@@ -14,6 +14,8 @@
 // accumulation order per body differs: own shares first here, then the reactions).
 // Systems are handed out per group as in bpl_hermite_stream (fixed steps only).
 #pragma once
+#include <algorithm>
+
 #include "hermite.cuh"
 
 namespace swarm {
@@ -401,6 +403,12 @@ cudaError_t launch_hermite_block_n(const BinView &B, int nunits, const StepParam
     *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
+  {  // the form is chosen by rule, not by the autotuner: run it at its design occupancy
+    // (two warps per sub-partition) even where a tuned grid asks for fewer CTAs
+    const long long S = B.list ? B.nlist : B.S;
+    const long long want = std::min<long long>((long long)BlockRing<N>::CPS * block_ring_sms(), (S + BlockRing<N>::G - 1) / BlockRing<N>::G);
+    if (grid < want) grid = (int)want;
+  }
   hermite_block_kernel<N><<<grid, BlockRing<N>::T, BlockRing<N>::BYTES, st>>>(B, nunits, P);
   return cudaGetLastError();
 }

@@ -260,6 +260,12 @@ cudaError_t launch_rkck_block_n(const BinView &B, int nunits, const StepParams &
     *blocks = nb;
   }
   if (grid <= 0) return cudaSuccess;
+  {  // the form is chosen by rule, not by the autotuner: run it at its design occupancy
+    // (two warps per sub-partition) even where a tuned grid asks for fewer CTAs
+    const long long S = B.list ? B.nlist : B.S;
+    const long long want = std::min<long long>((long long)BlockRingA<N>::CPS * block_ring_sms(), (S + BlockRingA<N>::G - 1) / BlockRingA<N>::G);
+    if (grid < want) grid = (int)want;
+  }
   rkck_block_kernel<N><<<grid, BlockRingA<N>::T, BlockRingA<N>::BYTES, st>>>(B, nunits, P);
   return cudaGetLastError();
 }
