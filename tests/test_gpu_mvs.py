@@ -235,3 +235,22 @@ def test_chunked_call_keeps_log_records_in_place(kind):
         assert len(lg) == o["log_count"][s] == 2
         np.testing.assert_allclose(lg[:, 0], o["log"][s, :2, 0], rtol=1e-14)
         np.testing.assert_allclose(lg[:, 1:], o["log"][s, :2, 1:], rtol=1e-9, atol=1e-14)
+
+
+@pytest.mark.parametrize("kind", [O.MVS_DH, O.MVS_JACOBI])
+def test_chunked_call_with_systems_at_different_times(kind):
+    # half the systems start 500 steps later than the others: the 3000-step call runs in
+    # chunks sized on the longest span, the later half finishing its 2500 steps on the way;
+    # against the oracle, which steps each system from its own time
+    ens = ics.mvs_compact(24, seed=18, k_lo=14.0, k_hi=20.0, m_lo=1e-5, m_hi=1e-4)
+    S_ = len(ens["n_body"])
+    time = np.where(np.arange(S_) % 2 == 0, 0.0, 500 * DT)
+    status = np.zeros(S_, dtype=np.int32)
+    T = 3000 * DT
+    o = run_oracle(ens, T, kind, DT, ce=3.0, ej=100.0, time=time, status=status)
+    sens = np.maximum(oracle_sensitivity(ens, T, kind, DT, ce=3.0, ej=100.0, time=time, status=status),
+                      3000 ** 1.5 * 2.0 ** -53)
+    g = run_gpu(ens, T, kind, DT, ce=3.0, ej=100.0, time=time, status=status)
+    assert g["stats"]["kernel_launches"] == 2 * 3
+    assert np.all(o["status"] == 1)
+    assert_parity(ens, g, o, sens=sens, steps=3000, max_relaxed=1.0)
