@@ -12,6 +12,15 @@
 
 namespace swarm {
 
+// a where p, else b, by masks on the bit patterns: integer instructions only, and no
+// branch the compiler could split the warp on
+__device__ __forceinline__ double selm(bool p, double a, double b) {
+  const long long mk = -(long long)p;
+  return __longlong_as_double((__double_as_longlong(a) & mk) | (__double_as_longlong(b) & ~mk));
+}
+// one of three values by m = rho mod 3
+__device__ __forceinline__ double sel3(int m, double a, double b, double c) { return selm(m == 0, a, selm(m == 1, b, c)); }
+
 // ---------------------------------------------------------------- acceleration ring
 // Acceleration only (Eq. 1), over M members at lanes base+OFF .. base+OFF+M-1; member j.
 // Lanes outside the members (the centre-of-mass lane in DH) mirror member 0 and their
@@ -123,6 +132,52 @@ __device__ __forceinline__ void ring_acc_rep(const F64k &k, const double (&x)[3]
       const double rs = shfl(sis[sl], src + q);
 #pragma unroll
       for (int c = 0; c < 3; c++) a[c] = fma(-rs, rdx[c], a[c]);
+    }
+    d2[r - 1] = shfl(r2s[sl], src + j);
+  }
+}
+
+// The same with each lane accumulating one component cc of its acceleration (the Jacobi
+// map that follows needs only that one on the lane, spread mode with R >= 3): the rounds'
+// terms are gathered as in ring_acc_rep and the component's FMAs run in the same order,
+// so ac has the bits of ring_acc_rep's a[cc].
+template <int M, int OFF, int NG, int R>
+__device__ __forceinline__ void ring_acc_rep_c(const F64k &k, const double (&x)[3], double m, int j, int base, int rho,
+                                               int g0, int cc, double &ac, double (&d2)[ARing<M>::RTA]) {
+  constexpr int RF = ARing<M>::RF, RT = ARing<M>::RT;
+  constexpr int NS = (RT + R - 1) / R;  // rounds per replica
+  double dxs[NS][3], sps[NS], sis[NS], r2s[NS];
+#pragma unroll
+  for (int sl = 0; sl < NS; sl++) {
+    const int r = rho + 1 + sl * R;
+    int p = j + r;
+    while (p >= M) p -= M;
+#pragma unroll
+    for (int c = 0; c < 3; c++) dxs[sl][c] = ksub(k, shfl(x[c], base + OFF + p), x[c]);
+    const double mp = shfl(m, base + OFF + p);
+    double r2 = kmul(k, dxs[sl][0], dxs[sl][0]);
+    r2 = fma(dxs[sl][1], dxs[sl][1], r2);
+    r2 = fma(dxs[sl][2], dxs[sl][2], r2);
+    const double rh = rsqrt(r2);
+    const double rho3 = kmul(k, kmul(k, rh, rh), rh);
+    sps[sl] = kmul(k, mp, rho3);
+    sis[sl] = kmul(k, m, rho3);
+    r2s[sl] = r2;
+  }
+  ac = 0.0;
+#pragma unroll
+  for (int r = 1; r <= RT; r++) {
+    const int sl = (r - 1) / R;
+    const int src = (g0 + (r - 1) % R) * NG + OFF;
+    const double dx = sel3(cc, shfl(dxs[sl][0], src + j), shfl(dxs[sl][1], src + j), shfl(dxs[sl][2], src + j));
+    const double sp = shfl(sps[sl], src + j);
+    ac = fma(sp, dx, ac);
+    if (r <= RF) {
+      int q = j - r;
+      if (q < 0) q += M;
+      const double rdx = sel3(cc, shfl(dxs[sl][0], src + q), shfl(dxs[sl][1], src + q), shfl(dxs[sl][2], src + q));
+      const double rs = shfl(sis[sl], src + q);
+      ac = fma(-rs, rdx, ac);
     }
     d2[r - 1] = shfl(r2s[sl], src + j);
   }
@@ -342,14 +397,6 @@ __device__ __forceinline__ bool kepler_drift(const F64k k, bool on, const KepCon
 // instruction costs the FP64 pipe its full time whatever its lanes compute, so for a
 // system alone in its warp this shortens the step: 31 fewer FP64 instructions per drift,
 // against 17 gathers and the selects (8-body Jacobi system alone: 10.2 -> 9.9 us per step).
-// a where p, else b, by masks on the bit patterns: integer instructions only, and no
-// branch the compiler could split the warp on
-__device__ __forceinline__ double selm(bool p, double a, double b) {
-  const long long mk = -(long long)p;
-  return __longlong_as_double((__double_as_longlong(a) & mk) | (__double_as_longlong(b) & ~mk));
-}
-// one of three values by m = rho mod 3
-__device__ __forceinline__ double sel3(int m, double a, double b, double c) { return selm(m == 0, a, selm(m == 1, b, c)); }
 
 // both Stumpff functions: replica 1 sums the c3 series, the others the c2 series (the
 // Horner steps of stumpff23), then every lane takes both and applies the quartering
@@ -604,22 +651,44 @@ __device__ __forceinline__ void mvs_acc(const F64k &fk, const double (&q)[3], do
       Q[c] = q[c];
     }
   } else {
-    jacobi_helio<N>(fk, q, w, b, Q);
-    double a[3];
-    if constexpr (R == 1) ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
-    else ring_acc_rep<N, 0, N, R>(fk, Q, m, b, base, rho, g0, a, d2);
-    double rho;
-    if (RQ) {
-      rho = rq;
-    } else {
-      rho = rsqrt(fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0]))));
-      rq = rho;
-    }
-    const double k = kmul(fk, kmul(fk, kmul(fk, mu, rho), rho), rho);
+    // R >= 3 (spread mode): each replica maps one component (m3 = rho mod 3) and the
+    // three are gathered, the same operations as jacobi_helio and the loop below
+    const int m3 = rho % 3, rep0 = g0 * N + b;
+    (void)m3;
+    (void)rep0;
+    if constexpr (R >= 3) {
+      const double qc = sel3(m3, q[0], q[1], q[2]);
+      const double pre = grp_scan_excl<N>(fk, b == 0 ? 0.0 : kmul(fk, w, qc), b);
+      const double Qc = b == 0 ? 0.0 : kadd(fk, qc, pre);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      double pre = grp_scan_excl<N>(fk, kmul(fk, m, a[c]), b);
-      acc[c] = b == 0 ? 0.0 : fma(-pre, eta_prev_inv, fma(k, q[c], a[c]));
+      for (int c = 0; c < 3; c++) Q[c] = shfl(Qc, rep0 + c * N);
+    } else {
+      jacobi_helio<N>(fk, q, w, b, Q);
+    }
+    double a[3] = {0.0, 0.0, 0.0}, ac = 0.0;  // R >= 3: the lane's component m3 only, in ac
+    if constexpr (R == 1) ring_acc<N, 0>(fk, Q, m, b, base, a, d2);
+    else if constexpr (R >= 3) ring_acc_rep_c<N, 0, N, R>(fk, Q, m, b, base, rho, g0, m3, ac, d2);
+    else ring_acc_rep<N, 0, N, R>(fk, Q, m, b, base, rho, g0, a, d2);
+    double iq;  // 1/|q|
+    if (RQ) {
+      iq = rq;
+    } else {
+      iq = rsqrt(fma(q[2], q[2], fma(q[1], q[1], kmul(fk, q[0], q[0]))));
+      rq = iq;
+    }
+    const double k = kmul(fk, kmul(fk, kmul(fk, mu, iq), iq), iq);
+    if constexpr (R >= 3) {
+      const double qc = sel3(m3, q[0], q[1], q[2]);
+      const double pre = grp_scan_excl<N>(fk, kmul(fk, m, ac), b);
+      const double av = b == 0 ? 0.0 : fma(-pre, eta_prev_inv, fma(k, qc, ac));
+#pragma unroll
+      for (int c = 0; c < 3; c++) acc[c] = shfl(av, rep0 + c * N);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double pre = grp_scan_excl<N>(fk, kmul(fk, m, a[c]), b);
+        acc[c] = b == 0 ? 0.0 : fma(-pre, eta_prev_inv, fma(k, q[c], a[c]));
+      }
     }
   }
 }
