@@ -662,7 +662,7 @@ static int run_persistent(swarm_ensemble *e, const StepParams &P0, int integrato
     // sub-partition) unless set.  Such calls end with a few long-lived systems whose step
     // latency alone sets the time, and a second warp on their sub-partition doubles it
     // (16384 x 8 compact ensemble, chunked calls: 1e4 steps 189 ms at one CTA per SM, 213
-    // at two; 1e5 steps 1.15 s against 1.64 s; 5000 steps even); shorter calls take the
+    // at two; 1e5 steps 1.04 s against 1.43 s; 5000 steps even); shorter calls take the
     // tuner's choice (over 2000 steps 2-3 CTAs per SM are ahead, 1.88e8 against 1.64e8
     // system-steps/s, as the FP64 pipe goes from 73 to 91 %).
     if ((integrator == SWARM_MVS_DH || integrator == SWARM_MVS_JACOBI) && !e->ctas_per_sm) {
