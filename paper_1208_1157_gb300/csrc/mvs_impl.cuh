@@ -989,7 +989,20 @@ __device__ __forceinline__ bool mvs_stream_step(const BinView &B, const StepPara
   if (active) L.kg++;
   const double h = (active && L.kg == L.plan.N && !L.plan.exact) ? L.plan.h_last : P.dt;
   const double hh = 0.5 * h;
-  if (!JAC) {
+  // DH spread over R >= 3 replicas: each replica runs the Cartesian drifts, the second
+  // kick and the acceleration's accumulation on one component (m3) and the results are
+  // gathered (the same operations, the same bits)
+  constexpr bool DHS = !JAC && R >= 3;
+  const int m3 = rho % 3, rep0 = g0 * N + b;
+  (void)m3;
+  (void)rep0;
+  if constexpr (DHS) {
+    const double uc = sel3(m3, L.u[0], L.u[1], L.u[2]), qc = sel3(m3, L.q[0], L.q[1], L.q[2]);
+    const double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, uc), b, base);
+    const double qn = b == 0 ? fma(hh, uc, qc) : fma(kmul(P.fk, hh, L.m0inv), ps, qc);
+#pragma unroll
+    for (int c = 0; c < 3; c++) L.q[c] = shfl(qn, rep0 + c * N);
+  } else if (!JAC) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, L.u[c]), b, base);
@@ -1012,15 +1025,32 @@ __device__ __forceinline__ bool mvs_stream_step(const BinView &B, const StepPara
   double Q[3], d2[RTA];
 #pragma unroll
   for (int r = 0; r < RTA; r++) d2[r] = 0.0;
-  mvs_acc<N, JAC, JAC, R>(P.fk, L.q, L.m, L.w, L.eta_prev_inv, L.mu, b, base, L.acc, Q, d2, L.rq, rho, g0);
-#pragma unroll
-  for (int c = 0; c < 3; c++) L.u[c] = fma(hh, L.acc[c], L.u[c]);
-  if (!JAC) {
+  if constexpr (DHS) {
+    double ac;
+    ring_acc_rep_c<N - 1, 1, N, R>(P.fk, L.q, L.m, b == 0 ? 0 : b - 1, base, rho, g0, m3, ac, d2);
+    if (b == 0) ac = 0.0;
+    const double un = fma(hh, ac, sel3(m3, L.u[0], L.u[1], L.u[2]));
+    const double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, un), b, base);
+    const double qc = sel3(m3, L.q[0], L.q[1], L.q[2]);
+    const double qn = b == 0 ? fma(hh, un, qc) : fma(kmul(P.fk, hh, L.m0inv), ps, qc);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, L.u[c]), b, base);
-      L.q[c] = b == 0 ? fma(hh, L.u[c], L.q[c]) : fma(kmul(P.fk, hh, L.m0inv), ps, L.q[c]);
+      L.acc[c] = shfl(ac, rep0 + c * N);
+      L.u[c] = shfl(un, rep0 + c * N);
+      L.q[c] = shfl(qn, rep0 + c * N);
       Q[c] = L.q[c];
+    }
+  } else {
+    mvs_acc<N, JAC, JAC, R>(P.fk, L.q, L.m, L.w, L.eta_prev_inv, L.mu, b, base, L.acc, Q, d2, L.rq, rho, g0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) L.u[c] = fma(hh, L.acc[c], L.u[c]);
+    if (!JAC) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        double ps = grp_sum<N>(P.fk, b == 0 ? 0.0 : kmul(P.fk, L.m, L.u[c]), b, base);
+        L.q[c] = b == 0 ? fma(hh, L.u[c], L.q[c]) : fma(kmul(P.fk, hh, L.m0inv), ps, L.q[c]);
+        Q[c] = L.q[c];
+      }
     }
   }
   // monitor on the heliocentric positions at the end of the step (R > 1: each replica
