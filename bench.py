@@ -735,23 +735,26 @@ def ncu_case(name):
     stream = torch.cuda.current_stream()
     from paper_1208_1157_gb300 import tune
     S.tuner_load(tune.DEFAULT_PATH)
-    if name == "io":  # checkpoint I/O of the paper-shaped ensemble: set_state + state query, 3 times
+    if name in ("io", "io_large"):  # checkpoint I/O: set_state + state query, 3 times
         import numpy as np
 
-        ens = ics.three_body(N_SYS, seed=2)
+        # io: the paper-shaped ensemble (the state fits in L2); io_large: 16x as many
+        # systems (2^21 x 3, 330 MB of state), a transfer long enough for steady bandwidth
+        ns = N_SYS if name == "io" else 16 * N_SYS
+        ens = ics.three_body(ns, seed=2)
         pos = torch.empty((len(ens["mass"]), 3), dtype=torch.float64, pin_memory=True).numpy()
         vel = torch.empty_like(torch.from_numpy(pos)).pin_memory().numpy()
-        # the same bytes moved by a plain elementwise kernel (read a, write b = 1.0 * a:
-        # 18.9 MB each way): the ceiling for a transfer of this size
+        # the same bytes moved by a plain elementwise kernel (read a, write b = 1.0 * a):
+        # the ceiling for a transfer of this size
         a = torch.ones(len(ens["mass"]) * 6, dtype=torch.float64, device="cuda")
         b = torch.empty_like(a)
         with S.Ensemble(ens, stream=stream) as e:
             for _ in range(3):
                 e.set_state(ens["pos"], ens["vel"])
-                e.state_into(pos, vel, np.empty(N_SYS), np.empty(N_SYS, np.int32))
+                e.state_into(pos, vel, np.empty(ns), np.empty(ns, np.int32))
                 torch.mul(a, 1.0, out=b)
         torch.cuda.synchronize()
-        log(f"ncu case io: {N_SYS} systems x {N_BODY} bodies")
+        log(f"ncu case {name}: {ns} systems x {N_BODY} bodies")
         return
     ctas = 0
     if name in ("hermite", "hermite_bpl", "plain"):
@@ -807,7 +810,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--ncu-case", help="hermite, hermite_bpl, plain, mvs, mvs_2cta, ragged, ragged_bin<n>, rkck, wide, "
-                    "hermite_adaptive, rkck_adaptive or io")
+                    "hermite_adaptive, rkck_adaptive, io or io_large")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
